@@ -1,0 +1,429 @@
+"""Benchmark: compressed NMF on one GB300 (and N-GPU replicas).
+
+Workload (one "step"): the large compressed-NMF configuration -- A = X0 Y0 +
+|N(0, 0.01^2)|, m = 20000, n = 10000, r = 20, FP32 storage; two-sided
+compression with d = 30, q = 4 (Alg. 1 on A and A^T, 2q + 2 = 10 reads of
+A), then 500 compressed ADMM sweeps (Alg. 4).  Inputs are synthetic and
+seeded, resident in HBM when the timed region starts; A (800 MB) is larger
+than L2, so no flush is needed between steps.
+
+The JSON line reports factorizations/s (value), the end-to-end figure
+through the public API with host buffers (e2e), time to the residual
+target against the uncompressed ADMM on the same GPU, the sketch kernel's
+roofline, the FP64 oracle timed on the host cores (cpu_baseline), sampled
+SM clocks, and the number of library kernel launches.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+CFG = dict(m=20000, n=10000, r=20, d=30, q=4, iters=500, sigma=0.01)
+WORKLOAD = "cnmf_m20000_n10000_r20_d30_q4_admm500_fp32"
+METRIC = ("cNMF time-to-rel-residual 1e-3 vs plain NMF; sketch HBM GB/s vs "
+          "peak; served p99")
+SEEDS = dict(data=1001, sketch=2001, init=3001)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm=d.get("hbm_gbs", 6800.0), src="measured",
+                    sm_max_mhz=d.get("sm_max_mhz", 2070.0))
+    return dict(hbm=6800.0, src="fallback", sm_max_mhz=2070.0)
+
+
+def _inputs():
+    A = synth.lowrank(CFG["m"], CFG["n"], CFG["r"], CFG["sigma"], SEEDS["data"],
+                      dtype=np.float32)
+    U0, V0 = synth.init_factors(CFG["m"], CFG["n"], CFG["r"], SEEDS["init"])
+    return A, U0.astype(np.float32), np.ascontiguousarray(V0.T).astype(np.float32)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 8:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(f[1]) for f in rows if f[1].replace(".", "").isdigit()]
+        mx = [float(f[2]) for f in rows if f[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = sorted({names[i] for f in rows for i in range(4)
+                          if f[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_sample(iters_sample=40):
+    """The FP64 oracle on the full workload: compression + `iters_sample`
+    ADMM sweeps, timed, and scaled to one factorization (compression + 500
+    sweeps).  Returns (factorizations/s, seconds, description)."""
+    from oracle import admm, compress, philox
+    A, U0, Vt0 = _inputs()
+    A64 = A.astype(np.float64)
+    m, n, r, d, q = CFG["m"], CFG["n"], CFG["r"], CFG["d"], CFG["q"]
+    Om, Ps = philox.test_matrices(SEEDS["sketch"], m, n, d)
+    t0 = time.perf_counter()
+    L, Rt, _, At = compress.compress(A64, Om, Ps, q)
+    t1 = time.perf_counter()
+    lam = float(np.linalg.norm(At)) / r
+    admm.admm(L, Rt, At, U0.astype(np.float64), Vt0.T.astype(np.float64),
+              lam=lam, phi=lam, iters=iters_sample)
+    t2 = time.perf_counter()
+    per_fact = (t1 - t0) + (t2 - t1) * CFG["iters"] / iters_sample
+    desc = (f"full workload compression ({t1 - t0:.2f} s) + {iters_sample} of "
+            f"{CFG['iters']} ADMM sweeps ({t2 - t1:.2f} s), scaled to one "
+            f"factorization")
+    return 1.0 / per_fact, (t2 - t0), desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; a timed step is one sample
+    t0 = time.perf_counter()
+    vals = []
+    desc = ""
+    for _ in range(args.steps):
+        v, _, desc = cpu_oracle_sample(iters_sample=20)
+        vals.append(v)
+    dt = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": "factorizations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "factorizations/s",
+                         "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "factorizations/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": dt,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def launches_per_step(q, chunks_gt1=True):
+    """Library kernel launches of one step (compress + one factor launch)."""
+    prod = 2 if chunks_gt1 else 1
+    per_pass = 2 * prod + 5          # A., A^T., CholeskyQR2 of both panels
+    compress = 2 + (2 * q + 1) * per_pass + prod + 2
+    return compress + 1
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true",
+                    help="skip the time-to-target measurement")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1505_04650_gb300 as cn
+    from paper_1505_04650_gb300 import build as cbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        cbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    m, n, r, d, q, iters = (CFG[k] for k in ("m", "n", "r", "d", "q", "iters"))
+    A_h, U0_h, Vt0_h = _inputs()
+    A = torch.from_numpy(A_h).to(dev)
+    U0 = torch.from_numpy(U0_h).to(dev)
+    Vt0 = torch.from_numpy(Vt0_h).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    lib = cn.lib()
+    ws_c = torch.empty(lib.cnmf_compress_workspace(m, n, d, 1), dtype=torch.uint8,
+                       device=dev)
+    ws_f = torch.empty(lib.cnmf_factor_workspace(m, n, r, d, 1), dtype=torch.uint8,
+                       device=dev)
+    U = U0.clone()
+    Vt = Vt0.clone()
+
+    # penalty: lambda = phi = ||Atilde||_F / r, fixed once from a first
+    # compression (host-side scalar, outside the timed region)
+    L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st,
+                                    ws=ws_c)
+    lam = cn.default_penalty(At, r)
+
+    def step():
+        L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st,
+                                        ws=ws_c)
+        U.copy_(U0)
+        Vt.copy_(Vt0)
+        cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
+        return L, Rt, At
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    cn.raise_on_status(st, "bench warm-up")
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    cn.raise_on_status(st, "bench timed region")
+    value = world * 1000.0 / ms
+
+    # ---- dominant kernel: the products with A (one per side per pass)
+    X = torch.randn(n, d, device=dev)
+    Y = torch.randn(m, d, device=dev)
+    for _ in range(3):
+        cn.cnmf_sketch_pass(A, X, Y)
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        cn.cnmf_sketch_pass(A, X, Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pass_ms = e0.elapsed_time(e1) / reps          # A X and A^T Y: two launches
+    flops_pass = 2 * 2.0 * m * n * d
+    bytes_pass = 2 * (4.0 * m * n + 4.0 * (m + n) * d)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = _peaks()
+    ffma_peak = nsm * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
+    achieved_tf = flops_pass / (pass_ms * 1e-3) / 1e12
+    achieved_gbs = bytes_pass / (pass_ms * 1e-3) / 1e9
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "factorizations/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "r": r, "d": d,
+                   "q": q, "admm_iters": iters, "lambda": lam,
+                   "l2": "inputs larger than L2 (A = 800 MB)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved_tf,
+                     "peak": ffma_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / ffma_peak, "traffic": None,
+                     "kernel": "k_prod (A X and A^T Y, FP32 FFMA)",
+                     "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 x "
+                                    f"{peaks['sm_max_mhz']:.0f} MHz",
+                     "hbm_gbs": achieved_gbs, "hbm_peak_gbs": peaks["hbm"],
+                     "hbm_frac": achieved_gbs / peaks["hbm"],
+                     "hbm_peak_source": peaks["src"],
+                     "ms_per_pass": pass_ms},
+        "clocks": clk.summary(),
+        "gpu_launches": launches_per_step(q) * args.steps,
+    }
+
+    # ---- end to end through the public API with host buffers
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    U_pin = torch.from_numpy(U0_h).pin_memory()
+    Vt_pin = torch.from_numpy(Vt0_h).pin_memory()
+    U_out = torch.empty_like(U_pin).pin_memory()
+    Vt_out = torch.empty_like(Vt_pin).pin_memory()
+
+    def e2e_step():
+        A.copy_(A_pin, non_blocking=True)
+        U.copy_(U_pin, non_blocking=True)
+        Vt.copy_(Vt_pin, non_blocking=True)
+        L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st,
+                                        ws=ws_c)
+        cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
+        U_out.copy_(U, non_blocking=True)
+        Vt_out.copy_(Vt, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ee0.elapsed_time(ee1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    out["e2e"] = {"value": world * 1000.0 / e2e_ms, "unit": "factorizations/s",
+                  "h2d_bytes_per_step": int(A_pin.numel() * 4 + U_pin.numel() * 4
+                                            + Vt_pin.numel() * 4),
+                  "d2h_bytes_per_step": int(U_out.numel() * 4 + Vt_out.numel() * 4),
+                  "ms_per_step": e2e_ms}
+
+    # ---- time to the residual target vs plain ADMM (same GPU)
+    if not args.no_ttt:
+        out["time_to_target"] = time_to_target(cn, A, U0, Vt0, lam, ws_c, ws_f,
+                                               st, stream)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, desc = cpu_oracle_sample()
+        out["cpu_baseline"] = {"value": v, "unit": "factorizations/s",
+                               "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": desc, "seconds": secs}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def time_to_target(cn, A, U0, Vt0, lam, ws_c, ws_f, st, stream):
+    """First sweep count k* with rho <= tau, tau = rho* + 1e-3 (rho* the
+    rank-r floor estimated from the singular values of A-tilde), then a
+    timed replay of compression + k* sweeps; the same for plain ADMM."""
+    import torch
+    m, n, r, d, q = CFG["m"], CFG["n"], CFG["r"], CFG["d"], CFG["q"]
+    L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st, ws=ws_c)
+    res = cn.cnmf_residual(A, U0, Vt0)
+    a2 = float(res[1].item())
+    s = torch.linalg.svdvals(At.double().cpu())
+    floor = float(np.sqrt(max(0.0, 1.0 - float((s[:r] ** 2).sum()) / a2)))
+    tau = floor + 1e-3
+    U, Vt = U0.clone(), Vt0.clone()
+    state = None
+    kstar, rho = None, None
+    for k in range(10, CFG["iters"] + 1, 10):
+        U, Vt, state, _ = cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, 10,
+                                         state=state, status=st, ws=ws_f)
+        res = cn.cnmf_residual(A, U, Vt)
+        rho = float(np.sqrt(res[0].item() / res[1].item()))
+        if rho <= tau:
+            kstar = k
+            break
+    out = {"tau": tau, "floor_est": floor, "compressed": {"k": kstar, "rho": rho}}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    if kstar:
+        ts = []
+        for rep in range(4):
+            U.copy_(U0); Vt.copy_(Vt0)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st,
+                                            ws=ws_c)
+            cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, kstar, status=st, ws=ws_f)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                ts.append(ev[0].elapsed_time(ev[1]))
+        out["compressed"]["seconds"] = float(np.median(ts)) / 1e3
+    # plain ADMM: same penalty scale relative to its matrix (||A||_F / r)
+    lam_p = float(np.sqrt(a2)) / r
+    U, Vt = U0.clone(), Vt0.clone()
+    state = None
+    kp, rho_p = None, None
+    ws_p = torch.empty(cn.lib().cnmf_plain_workspace(m, n, r, 1), dtype=torch.uint8,
+                       device=A.device)
+    cap = 3000
+    for k in range(10, cap + 1, 10):
+        U, Vt, state, _ = cn.cnmf_factor_plain(A, U, Vt, lam_p, lam_p, 10,
+                                               state=state, status=st, ws=ws_p)
+        res = cn.cnmf_residual(A, U, Vt)
+        rho_p = float(np.sqrt(res[0].item() / res[1].item()))
+        if rho_p <= tau:
+            kp = k
+            break
+    out["plain"] = {"k": kp, "rho": rho_p, "cap": cap, "lambda": lam_p}
+    if kp:
+        ts = []
+        for rep in range(3):
+            U.copy_(U0); Vt.copy_(Vt0)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            cn.cnmf_factor_plain(A, U, Vt, lam_p, lam_p, kp, status=st, ws=ws_p)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                ts.append(ev[0].elapsed_time(ev[1]))
+        out["plain"]["seconds"] = float(np.median(ts)) / 1e3
+    if out["compressed"].get("seconds") and out["plain"].get("seconds"):
+        out["speedup_vs_plain"] = out["plain"]["seconds"] / out["compressed"]["seconds"]
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,259 @@
+/*
+ * cnmf.h -- C ABI of the GB300 compressed-NMF / compressed-SNMF library.
+ *
+ * Method: Tepper & Sapiro, "Compressed Nonnegative Matrix Factorization is
+ * Fast and Accurate".  The library implements the data-parallel hot path:
+ *   - structured random compression (Alg. 1, Sec. II) applied to A and A^T
+ *     (Sec. III), giving L (m x d) and R (d x n);
+ *   - the compressed ADMM NMF iteration (Alg. 4, App. B) and, as a baseline,
+ *     the same iteration with L = I, R = I (uncompressed ADMM, Sec. III);
+ *   - compressed separable NMF column selection (Alg. 3, steps 1-2) with the
+ *     successive projection algorithm on Q^T A (Sec. IV);
+ *   - the relative reconstruction error used in Sec. V.
+ *
+ * Conventions (all entry points):
+ *   - Matrices are row-major.  A is m x n with row pitch lda >= n elements.
+ *     Tall panels are stored with the long dimension first: L is m x d,
+ *     R is stored transposed as Rt = R^T (n x d), V as Vt = V^T (n x r),
+ *     Phi as Phit = Phi^T (n x r), Rhat as Rhat_t = (Q^T A)^T (n x d).
+ *   - Every pointer is a DEVICE pointer owned by the caller, unless stated.
+ *     The library never allocates device memory and keeps no global mutable
+ *     state; scratch space is the caller's workspace `ws`, whose size comes
+ *     from the matching *_workspace() query (256-byte aligned pointer).
+ *   - All work is enqueued asynchronously on `stream` (a cudaStream_t).
+ *   - Host-detected errors (bad sizes, NULL pointers, small workspace,
+ *     launch failures) are returned immediately with NOTHING enqueued,
+ *     except CNMF_E_CUDA from a failed launch after earlier launches.
+ *   - Device-detected errors are written to *dev_status (device int32 that
+ *     the caller zeroes; the first error wins): CNMF_E_CHOLESKY (a Gram
+ *     matrix that is not numerically positive definite), CNMF_E_NONFINITE
+ *     (NaN/Inf met in a panel or factor), CNMF_E_TIMEOUT (a bounded grid
+ *     barrier wait expired; the kernel returns instead of hanging).
+ *     The caller reads *dev_status after synchronising the stream.
+ *   - Working precision W: FP64 when the input type is CNMF_F64, else FP32.
+ *     Outputs and test matrices are in W.  A stored as CNMF_BF16 is widened
+ *     to FP32 on load.
+ *   - Same inputs and seed give bitwise-identical outputs (all reductions
+ *     run in a fixed order; no floating-point atomics).
+ */
+#ifndef CNMF_H
+#define CNMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cnmf_stream_t; /* == cudaStream_t */
+
+typedef enum {
+  CNMF_OK = 0,
+  CNMF_E_INVALID_ARG = 1,
+  CNMF_E_WORKSPACE = 2,
+  CNMF_E_CUDA = 3,
+  CNMF_E_CHOLESKY = 4,
+  CNMF_E_NONFINITE = 5,
+  CNMF_E_TIMEOUT = 6
+} cnmf_status;
+
+/* Storage type of A (and, for CNMF_F64 / CNMF_F32, of W-typed buffers). */
+typedef enum { CNMF_F64 = 0, CNMF_F32 = 1, CNMF_BF16 = 2 } cnmf_dtype;
+
+/* Penalties lambda, phi and step xi of Alg. 4 (App. B); iters sweeps.
+ * The paper sets xi = 1 and leaves lambda, phi unspecified. */
+typedef struct {
+  double lambda;
+  double phi;
+  double xi;
+  int32_t iters;
+  int32_t barrier_timeout_ms; /* 0 -> default (2000 ms) */
+} cnmf_admm_params;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* cnmf_status_string(int32_t status);
+
+/* Detail of the CUDA error behind the calling thread's last CNMF_E_CUDA
+ * (error name, message, source location); "" if none.  Static per-thread
+ * buffer owned by the library. */
+const char* cnmf_last_error(void);
+
+/* ABI version of this header (bumped on incompatible change). */
+int32_t cnmf_abi_version(void);
+
+/* ------------------------------------------------------------------------
+ * Gaussian test matrices (Alg. 1, first step: Omega with i.i.d. N(0,1)).
+ * Counter-based: Philox4x32-10 (Salmon et al., SC'11) + Box-Muller.
+ * key = (seed mod 2^32, seed >> 32); counter = (b mod 2^32, b >> 32,
+ * stream_id, 0) for block b = e / 4 of row-major element e; uniforms
+ * u = (x + 0.5) 2^-32; (z0, z1) from words (0, 1), (z2, z3) from (2, 3);
+ * element e takes z_{e mod 4}.  Box-Muller is evaluated in FP64.
+ * ---------------------------------------------------------------------- */
+
+/* out: rows x cols (row-major) in out_type (CNMF_F64 or CNMF_F32). */
+cnmf_status cnmf_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows,
+                          int64_t cols, cnmf_dtype out_type, void* out,
+                          cnmf_stream_t stream);
+
+/* out: nblocks x 4 uint32 raw Philox words of blocks first_block.. . */
+cnmf_status cnmf_philox_words(uint64_t seed, uint32_t stream_id,
+                              int64_t first_block, int64_t nblocks,
+                              uint32_t* out, cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Building blocks of the compression (exposed for step-level checks).
+ * ---------------------------------------------------------------------- */
+
+/* One two-sided product pass over A (Alg. 1 power scheme, Sec. III):
+ *   Zm = A X   (m x k, from X n x k)     and/or
+ *   Zn = A^T Y (n x k, from Y m x k),
+ * reading A once per product.  X, Y, Zm, Zn are W-typed with row pitch k.
+ * Pass X = NULL / Zm = NULL (or Y = NULL / Zn = NULL) to skip one side.
+ * 1 <= k <= 128. */
+size_t cnmf_sketch_workspace(int64_t m, int64_t n, int32_t k,
+                             cnmf_dtype a_type);
+cnmf_status cnmf_sketch_pass(const void* A, cnmf_dtype a_type, int64_t m,
+                             int64_t n, int64_t lda, int32_t k, const void* X,
+                             const void* Y, void* Zm, void* Zn, void* ws,
+                             size_t ws_bytes, cnmf_stream_t stream);
+
+/* Orthonormal basis (Alg. 1, last step: "QR decomposition") of a tall
+ * panel Y (rows x k, W-typed, row pitch k, rows >= k), in place:
+ * CholeskyQR2 with FP64-accurate Gram matrices (double-float accumulation
+ * on FP32 data) and a small diagonal shift in the first sweep.  The result
+ * equals the thin Q of Y with diag(R) > 0 (unique for full column rank). */
+size_t cnmf_orth_workspace(int64_t rows, int32_t k, cnmf_dtype w_type);
+cnmf_status cnmf_orth(void* Y, cnmf_dtype w_type, int64_t rows, int32_t k,
+                      void* ws, size_t ws_bytes, int32_t* dev_status,
+                      cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cnmf_compress: two-sided structured random compression (Alg. 1 on A and
+ * A^T, Sec. III) with q power iterations and re-orthonormalisation after
+ * every product, then A-tilde = L^T A R^T (Alg. 4 setup).
+ *   A       m x n, a_type, pitch lda (>= n).  NMF expects A >= 0 (Sec. I);
+ *           negative entries are not rejected.
+ *   r, d    target rank and sketch size d = r + r_ov, 1 <= r <= d <=
+ *           min(m, n), d <= 128.
+ *   q       power iterations (Alg. 1 exponent w), 0 <= q <= 64.  The
+ *           compression reads A 2q + 2 times.
+ *   seed    Philox seed for Omega (stream 0, n x d, left chain) and Psi
+ *           (stream 1, m x d, right chain), used when Omega/Psi are NULL.
+ *   Omega, Psi  optional caller test matrices (W-typed, n x d and m x d).
+ *   L       out, m x d, orthonormal columns.
+ *   Rt      out, n x d, R^T (R has orthonormal rows).
+ *   Atilde  out, d x d.
+ * ---------------------------------------------------------------------- */
+size_t cnmf_compress_workspace(int64_t m, int64_t n, int32_t d,
+                               cnmf_dtype a_type);
+cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type, int64_t m,
+                          int64_t n, int64_t lda, int32_t r, int32_t d,
+                          int32_t q, uint64_t seed, const void* Omega,
+                          const void* Psi, void* L, void* Rt, void* Atilde,
+                          void* ws, size_t ws_bytes, int32_t* dev_status,
+                          cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cnmf_factor: `p->iters` sweeps of compressed ADMM (Alg. 4, App. B):
+ *   Xt <- (Atilde Yt^T + lam L^T U - L^T Lam)(Yt Yt^T + lam I)^-1
+ *   Yt <- (Xt^T Xt + phi I)^-1 (Xt^T Atilde + phi V R^T - Phi R^T)
+ *   U  <- P+(L Xt + Lam/lam),  V <- P+(Yt R + Phi/phi)
+ *   Lam <- Lam + xi lam (L Xt - U),  Phi <- Phi + xi phi (Yt R - V)
+ * One persistent cooperative launch; grid barriers are bounded.
+ *   L (m x d), Rt (n x d), Atilde (d x d): from cnmf_compress (W-typed).
+ *   U   in/out m x r.  On a fresh start (resume = 0): the initial U.
+ *   Vt  in/out n x r (V^T).  On a fresh start: the initial V^T.
+ *   state  in/out, cnmf_factor_state_bytes() bytes, W-typed sections in
+ *          this order: Lam (m x r), Phit (n x r), Yt (r x d), Xt (d x r),
+ *          then int64 k (sweeps done so far) at the next 8-byte boundary.
+ *          resume = 0: Yt <- V R^T, Lam = Phi = 0, k = 0 (Alg. 4 setup).
+ *          resume = 1: continue from the state; the result is bitwise the
+ *          same as an uninterrupted run.
+ *   1 <= r <= d <= 128, r <= 64, lambda, phi > 0.
+ * ---------------------------------------------------------------------- */
+size_t cnmf_factor_workspace(int64_t m, int64_t n, int32_t r, int32_t d,
+                             cnmf_dtype w_type);
+size_t cnmf_factor_state_bytes(int64_t m, int64_t n, int32_t r, int32_t d,
+                               cnmf_dtype w_type);
+cnmf_status cnmf_factor(const void* L, const void* Rt, const void* Atilde,
+                        cnmf_dtype w_type, int64_t m, int64_t n, int32_t r,
+                        int32_t d, const cnmf_admm_params* p, void* U,
+                        void* Vt, void* state, int32_t resume, void* ws,
+                        size_t ws_bytes, int32_t* dev_status,
+                        cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cnmf_factor_plain: the uncompressed ADMM NMF baseline -- Alg. 4 with
+ * L = I_m, R = I_n, Atilde = A (Sec. III, problem nmfEquiv; Xu et al.).
+ * Each sweep reads A twice (A Y^T, then A^T X with the new X).
+ *   A, a_type, m, n, lda as in cnmf_compress; W from a_type.
+ *   U in/out m x r; Vt in/out n x r.
+ *   state  cnmf_plain_state_bytes(): Lam (m x r), Phit (n x r), Yt (n x r,
+ *          = Y^T), X (m x r), then int64 k.  resume as in cnmf_factor.
+ * ---------------------------------------------------------------------- */
+size_t cnmf_plain_workspace(int64_t m, int64_t n, int32_t r,
+                            cnmf_dtype a_type);
+size_t cnmf_plain_state_bytes(int64_t m, int64_t n, int32_t r,
+                              cnmf_dtype a_type);
+cnmf_status cnmf_factor_plain(const void* A, cnmf_dtype a_type, int64_t m,
+                              int64_t n, int64_t lda, int32_t r,
+                              const cnmf_admm_params* p, void* U, void* Vt,
+                              void* state, int32_t resume, void* ws,
+                              size_t ws_bytes, int32_t* dev_status,
+                              cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * snmf_select: compressed separable NMF, Alg. 3 steps 1-2 (Sec. IV).
+ *   Q = Alg.1(A) with q power iterations (one-sided, 2q + 1 products,
+ *   re-orthonormalised after each), Rhat = Q^T A (d x n), then the
+ *   successive projection algorithm on the columns of Rhat: r times pick
+ *   j* = argmax_j ||Rhat[:, j]||^2 (ties -> lowest j), u = Rhat[:, j*] /
+ *   ||.||, Rhat <- (I - u u^T) Rhat.
+ *   Omega  optional n x d W-typed test matrix (else Philox stream 0).
+ *   anchors  out, r int64 column indices in selection order.
+ *   Rhat_t   optional out, n x d (= Rhat^T) BEFORE the SPA projections.
+ *   1 <= r <= d <= min(m, n), d <= 128.
+ * ---------------------------------------------------------------------- */
+size_t snmf_select_workspace(int64_t m, int64_t n, int32_t d,
+                             cnmf_dtype a_type);
+cnmf_status snmf_select(const void* A, cnmf_dtype a_type, int64_t m,
+                        int64_t n, int64_t lda, int32_t r, int32_t d,
+                        int32_t q, uint64_t seed, const void* Omega,
+                        int64_t* anchors, void* Rhat_t, void* ws,
+                        size_t ws_bytes, int32_t* dev_status,
+                        cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cnmf_residual: out2[0] = ||A - U V||_F^2, out2[1] = ||A||_F^2 (FP64,
+ * device), in one read of A (Sec. V reports sqrt(out2[0] / out2[1])).
+ *   U m x r, Vt n x r in w_type (CNMF_F64 or CNMF_F32), 1 <= r <= 128.
+ * ---------------------------------------------------------------------- */
+size_t cnmf_residual_workspace(int64_t m, int64_t n, int32_t r,
+                               cnmf_dtype a_type);
+cnmf_status cnmf_residual(const void* A, cnmf_dtype a_type, int64_t m,
+                          int64_t n, int64_t lda, const void* U,
+                          const void* Vt, cnmf_dtype w_type, int32_t r,
+                          double* out2, void* ws, size_t ws_bytes,
+                          cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cnmf_barrier_selftest: exercises the bounded grid barrier that the
+ * persistent kernels (cnmf_factor) use.  A cooperative grid of `ctas` CTAs
+ * (<= SM count) passes `rounds` barriers.  If 0 <= skip < ctas, CTA `skip`
+ * leaves before the first barrier, so the others can never complete it:
+ * they give up after timeout_ms (1..10000), write CNMF_E_TIMEOUT to
+ * *dev_status and return -- nothing hangs.  With skip < 0 every barrier
+ * completes and *dev_status stays 0.  *out_rounds (optional device int32)
+ * receives the number of barriers CTA 0 passed.  ws: >= 256 bytes.
+ * (Library self-test; the paper has no counterpart.)
+ * ---------------------------------------------------------------------- */
+cnmf_status cnmf_barrier_selftest(int32_t ctas, int32_t rounds, int32_t skip,
+                                  int32_t timeout_ms, void* ws,
+                                  size_t ws_bytes, int32_t* dev_status,
+                                  int32_t* out_rounds, cnmf_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CNMF_H */

@@ -1,0 +1,326 @@
+"""GB300-native compressed NMF / SNMF (Tepper & Sapiro, arXiv 1505.04650).
+
+Thin PyTorch-facing binding over the C ABI of ``libcnmf.so`` (see
+include/cnmf.h).  Each function only marshals arguments: it checks dtypes,
+shapes and devices, allocates outputs and the workspace with PyTorch on the
+tensors' CUDA device, and calls the entry point of the same name on the
+current CUDA stream.  Every step of the method runs in the library's CUDA
+kernels; if the library is missing the import of a function raises.
+
+Storage dtypes: float64 (FP64 path), float32, bfloat16 (A only; arithmetic
+in FP32).  Tall panels are row-major with the long dimension first
+(L m x d, Rt = R^T n x d, Vt = V^T n x r).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import AdmmParams
+
+__all__ = [
+    "CnmfError", "lib", "cnmf_gaussian", "cnmf_philox_words",
+    "cnmf_sketch_pass", "cnmf_orth", "cnmf_compress", "cnmf_factor",
+    "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
+    "sketch_size", "default_penalty",
+]
+
+
+class CnmfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        msg = lib().cnmf_status_string(self.code).decode()
+        if self.code == _lib.CNMF_E_CUDA:
+            msg += " -- " + lib().cnmf_last_error().decode()
+        super().__init__(f"{where}: {msg}")
+
+
+def lib():
+    return _lib.load()
+
+
+_DT = {torch.float64: _lib.CNMF_F64, torch.float32: _lib.CNMF_F32,
+       torch.bfloat16: _lib.CNMF_BF16}
+
+
+def _wdtype(a_dtype: torch.dtype) -> torch.dtype:
+    return torch.float64 if a_dtype == torch.float64 else torch.float32
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(dev):
+    return C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _check(code: int, where: str):
+    if code != _lib.CNMF_OK:
+        raise CnmfError(code, where)
+
+
+def _mat(A: torch.Tensor, name: str = "A"):
+    if A.dim() != 2 or A.dtype not in _DT or not A.is_cuda:
+        raise ValueError(f"{name} must be a 2-D CUDA float64/float32/bfloat16 tensor")
+    if A.stride(1) != 1 or A.stride(0) < A.shape[1]:
+        raise ValueError(f"{name} must be row-major with unit column stride")
+    return A.shape[0], A.shape[1], A.stride(0)
+
+
+def _dense(t: torch.Tensor, shape, dtype, name):
+    if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+    return t
+
+
+def _ws(nbytes: int, dev) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+def _status(dev):
+    return torch.zeros(1, dtype=torch.int32, device=dev)
+
+
+def raise_on_status(status: torch.Tensor, where: str):
+    """Synchronising check of a device status word (first error wins)."""
+    code = int(status.item())
+    if code != _lib.CNMF_OK:
+        raise CnmfError(code, where)
+
+
+def sketch_size(r: int, r_ov: int, n: int) -> int:
+    """The paper's rule d = min(max(20, r + r_ov), n) (Sec. V)."""
+    return min(max(20, r + r_ov), n)
+
+
+def default_penalty(Atilde: torch.Tensor, r: int) -> float:
+    """lambda = phi = ||Atilde||_F / r (the balanced reading of Alg. 4's
+    unspecified penalties; a host-side scalar from the compressed matrix)."""
+    return float(torch.linalg.norm(Atilde.double())) / r
+
+
+# --------------------------------------------------------------------------
+def cnmf_gaussian(seed: int, stream_id: int, rows: int, cols: int,
+                  dtype=torch.float32, device="cuda") -> torch.Tensor:
+    out = torch.empty(rows, cols, dtype=dtype, device=device)
+    _check(lib().cnmf_gaussian(seed, stream_id, rows, cols, _DT[dtype],
+                               _ptr(out), _stream(out.device)), "cnmf_gaussian")
+    return out
+
+
+def cnmf_philox_words(seed: int, stream_id: int, first_block: int,
+                      nblocks: int, device="cuda") -> torch.Tensor:
+    """Raw Philox4x32-10 output words, nblocks x 4 (int32 bit patterns)."""
+    out = torch.empty(nblocks, 4, dtype=torch.int32, device=device)
+    _check(lib().cnmf_philox_words(seed, stream_id, first_block, nblocks,
+                                   _ptr(out), _stream(out.device)),
+           "cnmf_philox_words")
+    return out
+
+
+def cnmf_sketch_pass(A: torch.Tensor, X: torch.Tensor | None = None,
+                     Y: torch.Tensor | None = None):
+    """(A X, A^T Y) with one read of A per product; either may be None."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    k = (X if X is not None else Y).shape[1]
+    if X is not None:
+        _dense(X, (n, k), w, "X")
+    if Y is not None:
+        _dense(Y, (m, k), w, "Y")
+    Zm = torch.empty(m, k, dtype=w, device=A.device) if X is not None else None
+    Zn = torch.empty(n, k, dtype=w, device=A.device) if Y is not None else None
+    L = lib()
+    nb = L.cnmf_sketch_workspace(m, n, k, _DT[A.dtype])
+    ws = _ws(nb, A.device)
+    _check(L.cnmf_sketch_pass(_ptr(A), _DT[A.dtype], m, n, lda, k, _ptr(X),
+                              _ptr(Y), _ptr(Zm), _ptr(Zn), _ptr(ws), nb,
+                              _stream(A.device)), "cnmf_sketch_pass")
+    return Zm, Zn
+
+
+def cnmf_orth(Y: torch.Tensor, status: torch.Tensor | None = None):
+    """In-place orthonormal basis of a tall panel (CholeskyQR2)."""
+    rows, k = Y.shape
+    if Y.dtype not in (torch.float64, torch.float32) or not Y.is_contiguous():
+        raise ValueError("Y must be contiguous float64/float32")
+    st = status if status is not None else _status(Y.device)
+    L = lib()
+    nb = L.cnmf_orth_workspace(rows, k, _DT[Y.dtype])
+    ws = _ws(nb, Y.device)
+    _check(L.cnmf_orth(_ptr(Y), _DT[Y.dtype], rows, k, _ptr(ws), nb, _ptr(st),
+                       _stream(Y.device)), "cnmf_orth")
+    return Y, st
+
+
+def cnmf_compress(A: torch.Tensor, r: int, d: int, q: int, seed: int,
+                  Omega: torch.Tensor | None = None,
+                  Psi: torch.Tensor | None = None,
+                  status: torch.Tensor | None = None, ws=None):
+    """Two-sided compression -> (L m x d, Rt n x d, Atilde d x d, status)."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    if Omega is not None:
+        _dense(Omega, (n, d), w, "Omega")
+    if Psi is not None:
+        _dense(Psi, (m, d), w, "Psi")
+    dev = A.device
+    Lm = torch.empty(m, d, dtype=w, device=dev)
+    Rt = torch.empty(n, d, dtype=w, device=dev)
+    At = torch.empty(d, d, dtype=w, device=dev)
+    st = status if status is not None else _status(dev)
+    L = lib()
+    nb = L.cnmf_compress_workspace(m, n, d, _DT[A.dtype])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(L.cnmf_compress(_ptr(A), _DT[A.dtype], m, n, lda, r, d, q, seed,
+                           _ptr(Omega), _ptr(Psi), _ptr(Lm), _ptr(Rt),
+                           _ptr(At), _ptr(ws), ws.numel(), _ptr(st),
+                           _stream(dev)), "cnmf_compress")
+    return Lm, Rt, At, st
+
+
+@dataclass
+class FactorState:
+    """Resumable ADMM state (device buffer in the ABI's layout)."""
+    buf: torch.Tensor
+    m: int
+    n: int
+    r: int
+    d: int          # 0 for the plain (uncompressed) baseline
+    dtype: torch.dtype
+
+    def _sections(self):
+        e = 8 if self.dtype == torch.float64 else 4
+        m, n, r, d = self.m, self.n, self.r, self.d
+        if self.d:
+            sizes = [("Lam", (m, r)), ("Phit", (n, r)), ("Yt", (r, d)),
+                     ("Xt", (d, r))]
+        else:
+            sizes = [("Lam", (m, r)), ("Phit", (n, r)), ("Yt", (n, r)),
+                     ("X", (m, r))]
+        out, off = {}, 0
+        for name, shp in sizes:
+            cnt = shp[0] * shp[1]
+            out[name] = self.buf[off:off + cnt * e].view(self.dtype).view(*shp)
+            off += cnt * e
+        out["k"] = self.buf[self.buf.numel() - 8:].view(torch.int64)
+        return out
+
+    def __getattr__(self, name):
+        if name in ("Lam", "Phit", "Yt", "Xt", "X", "k"):
+            return self._sections()[name]
+        raise AttributeError(name)
+
+
+def cnmf_factor(L: torch.Tensor, Rt: torch.Tensor, Atilde: torch.Tensor,
+                U: torch.Tensor, Vt: torch.Tensor, lam: float, phi: float,
+                iters: int, xi: float = 1.0, state: FactorState | None = None,
+                status: torch.Tensor | None = None,
+                barrier_timeout_ms: int = 0, ws=None):
+    """`iters` sweeps of compressed ADMM (Alg. 4); U (m x r), Vt (n x r)
+    are updated in place.  Returns (U, Vt, state, status)."""
+    m, d = L.shape
+    n = Rt.shape[0]
+    r = U.shape[1]
+    w = L.dtype
+    for t, shp, nm in ((L, (m, d), "L"), (Rt, (n, d), "Rt"),
+                       (Atilde, (d, d), "Atilde"), (U, (m, r), "U"),
+                       (Vt, (n, r), "Vt")):
+        _dense(t, shp, w, nm)
+    dev = L.device
+    lb = lib()
+    resume = 1
+    if state is None:
+        nbs = lb.cnmf_factor_state_bytes(m, n, r, d, _DT[w])
+        state = FactorState(torch.zeros(nbs, dtype=torch.uint8, device=dev),
+                            m, n, r, d, w)
+        resume = 0
+    st = status if status is not None else _status(dev)
+    nb = lb.cnmf_factor_workspace(m, n, r, d, _DT[w])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    p = AdmmParams(lam, phi, xi, iters, barrier_timeout_ms)
+    _check(lb.cnmf_factor(_ptr(L), _ptr(Rt), _ptr(Atilde), _DT[w], m, n, r, d,
+                          C.byref(p), _ptr(U), _ptr(Vt), _ptr(state.buf),
+                          resume, _ptr(ws), ws.numel(), _ptr(st),
+                          _stream(dev)), "cnmf_factor")
+    return U, Vt, state, st
+
+
+def cnmf_factor_plain(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,
+                      lam: float, phi: float, iters: int, xi: float = 1.0,
+                      state: FactorState | None = None,
+                      status: torch.Tensor | None = None, ws=None):
+    """Uncompressed ADMM NMF baseline (Alg. 4 with L = I, R = I)."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    r = U.shape[1]
+    _dense(U, (m, r), w, "U")
+    _dense(Vt, (n, r), w, "Vt")
+    dev = A.device
+    lb = lib()
+    resume = 1
+    if state is None:
+        nbs = lb.cnmf_plain_state_bytes(m, n, r, _DT[A.dtype])
+        state = FactorState(torch.zeros(nbs, dtype=torch.uint8, device=dev),
+                            m, n, r, 0, w)
+        resume = 0
+    st = status if status is not None else _status(dev)
+    nb = lb.cnmf_plain_workspace(m, n, r, _DT[A.dtype])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    p = AdmmParams(lam, phi, xi, iters, 0)
+    _check(lb.cnmf_factor_plain(_ptr(A), _DT[A.dtype], m, n, lda, r,
+                                C.byref(p), _ptr(U), _ptr(Vt),
+                                _ptr(state.buf), resume, _ptr(ws), ws.numel(),
+                                _ptr(st), _stream(dev)), "cnmf_factor_plain")
+    return U, Vt, state, st
+
+
+def snmf_select(A: torch.Tensor, r: int, d: int, q: int, seed: int,
+                Omega: torch.Tensor | None = None, return_rhat: bool = False,
+                status: torch.Tensor | None = None, ws=None):
+    """Alg. 3 steps 1-2 -> anchors (int64[r], selection order) [, Rhat_t]."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    dev = A.device
+    if Omega is not None:
+        _dense(Omega, (n, d), w, "Omega")
+    anchors = torch.empty(r, dtype=torch.int64, device=dev)
+    rh = torch.empty(n, d, dtype=w, device=dev) if return_rhat else None
+    st = status if status is not None else _status(dev)
+    lb = lib()
+    nb = lb.snmf_select_workspace(m, n, d, _DT[A.dtype])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(lb.snmf_select(_ptr(A), _DT[A.dtype], m, n, lda, r, d, q, seed,
+                          _ptr(Omega), _ptr(anchors), _ptr(rh), _ptr(ws),
+                          ws.numel(), _ptr(st), _stream(dev)), "snmf_select")
+    return (anchors, rh, st) if return_rhat else (anchors, st)
+
+
+def cnmf_residual(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,
+                  out: torch.Tensor | None = None, ws=None) -> torch.Tensor:
+    """Device FP64 pair (||A - U V||^2, ||A||^2)."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    r = U.shape[1]
+    _dense(U, (m, r), w, "U")
+    _dense(Vt, (n, r), w, "Vt")
+    dev = A.device
+    out = out if out is not None else torch.empty(2, dtype=torch.float64,
+                                                  device=dev)
+    lb = lib()
+    nb = lb.cnmf_residual_workspace(m, n, r, _DT[A.dtype])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(lb.cnmf_residual(_ptr(A), _DT[A.dtype], m, n, lda, _ptr(U),
+                            _ptr(Vt), _DT[w], r, _ptr(out), _ptr(ws),
+                            ws.numel(), _stream(dev)), "cnmf_residual")
+    return out

@@ -1,0 +1,124 @@
+// Status strings, ABI version and device queries.
+#include <cstdio>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace cnmf {
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    return 1;
+  }
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+        cudaSuccess)
+      (void)cudaGetLastError();
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+int max_smem_optin() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    return 48 * 1024;
+  }
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                               dev) != cudaSuccess)
+      (void)cudaGetLastError();
+    cached[dev] = v > 0 ? v : 48 * 1024;
+  }
+  return cached[dev];
+}
+
+size_t static_smem(const void* func) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return fa.sharedSizeBytes;
+}
+
+bool set_max_smem(const void* func, size_t bytes) {
+  if (bytes + static_smem(func) > (size_t)max_smem_optin()) return false;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+static thread_local char g_err[320];
+
+void record_cuda_error(cudaError_t e, const char* file, int line) {
+  const char* base = file;
+  for (const char* p = file; *p; ++p)
+    if (*p == '/') base = p + 1;
+  snprintf(g_err, sizeof(g_err), "%s (%s) at %s:%d", cudaGetErrorName(e),
+           cudaGetErrorString(e), base, line);
+}
+
+}  // namespace cnmf
+
+extern "C" const char* cnmf_last_error(void) { return cnmf::g_err; }
+
+extern "C" const char* cnmf_status_string(int32_t status) {
+  switch (status) {
+    case CNMF_OK: return "CNMF_OK";
+    case CNMF_E_INVALID_ARG: return "CNMF_E_INVALID_ARG: invalid argument";
+    case CNMF_E_WORKSPACE: return "CNMF_E_WORKSPACE: workspace too small";
+    case CNMF_E_CUDA: return "CNMF_E_CUDA: CUDA launch or runtime error";
+    case CNMF_E_CHOLESKY:
+      return "CNMF_E_CHOLESKY: Gram matrix not numerically positive definite";
+    case CNMF_E_NONFINITE: return "CNMF_E_NONFINITE: NaN or Inf encountered";
+    case CNMF_E_TIMEOUT: return "CNMF_E_TIMEOUT: grid barrier wait expired";
+    default: return "CNMF_E_UNKNOWN";
+  }
+}
+
+extern "C" int32_t cnmf_abi_version(void) { return 1; }
+
+// Self-test of the bounded grid barrier (see cnmf.h).
+namespace cnmf {
+__global__ void k_barrier_selftest(unsigned* bar, int rounds, int skip,
+                                   uint64_t timeout_ns, int32_t* status,
+                                   int32_t* out_rounds) {
+  int passed = 0;
+  for (int i = 0; i < rounds; ++i) {
+    if ((int)blockIdx.x == skip) return;   // this CTA never arrives
+    if (!grid_barrier(bar, status, timeout_ns)) break;
+    ++passed;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && out_rounds) *out_rounds = passed;
+}
+}  // namespace cnmf
+
+extern "C" cnmf_status cnmf_barrier_selftest(int32_t ctas, int32_t rounds,
+                                             int32_t skip, int32_t timeout_ms,
+                                             void* ws, size_t ws_bytes,
+                                             int32_t* dev_status,
+                                             int32_t* out_rounds,
+                                             cnmf_stream_t stream) {
+  if (ctas < 1 || ctas > cnmf::num_sms() || rounds < 0 || timeout_ms < 1 ||
+      timeout_ms > 10000 || !ws || ws_bytes < 256 || !dev_status)
+    return CNMF_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* bar = (unsigned*)ws;
+  CNMF_CUDA(cudaMemsetAsync(bar, 0, 256, s));
+  uint64_t tns = (uint64_t)timeout_ms * 1000000ull;
+  void* args[] = {&bar, &rounds, &skip, &tns, &dev_status, &out_rounds};
+  CNMF_CUDA(cudaLaunchCooperativeKernel((const void*)cnmf::k_barrier_selftest,
+                                        dim3(ctas), dim3(128), args, 0, s));
+  return CNMF_OK;
+}

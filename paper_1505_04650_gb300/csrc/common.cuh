@@ -1,0 +1,204 @@
+// Shared device/host helpers for the compressed-NMF library (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cnmf.h"
+
+namespace cnmf {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------------------
+// Element loads: A may be stored as double, float or bfloat16; arithmetic is
+// done in the working type W (double for FP64 inputs, float otherwise).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(bf16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ double to_f(double x) { return x; }
+
+template <typename W, typename T>
+__device__ __forceinline__ W widen(T x) {
+  return static_cast<W>(to_f(x));
+}
+
+// 4 consecutive elements from shared memory (16-, 8- or 32-byte aligned).
+template <typename W, typename T>
+__device__ __forceinline__ void lds4(const T* p, W out[4]);
+
+template <>
+__device__ __forceinline__ void lds4<float, float>(const float* p, float o[4]) {
+  float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds4<float, bf16>(const bf16* p, float o[4]) {
+  uint2 v = *reinterpret_cast<const uint2*>(p);
+  o[0] = __uint_as_float(v.x << 16);
+  o[1] = __uint_as_float(v.x & 0xFFFF0000u);
+  o[2] = __uint_as_float(v.y << 16);
+  o[3] = __uint_as_float(v.y & 0xFFFF0000u);
+}
+template <>
+__device__ __forceinline__ void lds4<double, double>(const double* p,
+                                                     double o[4]) {
+  double2 a = *reinterpret_cast<const double2*>(p);
+  double2 b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+// N consecutive W values from shared memory, vectorised when possible.
+template <int N, typename W>
+__device__ __forceinline__ void ldsN(const W* p, W* o) {
+  if constexpr (sizeof(W) == 4 && N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+      float4 v = *reinterpret_cast<const float4*>(p + i);
+      o[i] = v.x; o[i + 1] = v.y; o[i + 2] = v.z; o[i + 3] = v.w;
+    }
+  } else if constexpr (N % 2 == 0) {
+    typedef typename std::conditional<sizeof(W) == 4, float2, double2>::type V2;
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      V2 v = *reinterpret_cast<const V2*>(p + i);
+      o[i] = v.x; o[i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] = p[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cp.async (16-byte global -> shared copies, L2-only caching)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s),
+               "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// ---------------------------------------------------------------------------
+// Status word: the first device-detected error wins.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int32_t* st, int32_t code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Grid barrier for a cooperative (co-resident) grid, with a bounded wait.
+// bar[0] = arrival count, bar[1] = generation, bar[2] = abort flag.
+// Returns false when the grid must stop (timeout here or elsewhere); the
+// timeout sets CNMF_E_TIMEOUT in *status and raises the abort flag, so every
+// other CTA leaves its own wait promptly instead of spinning to its limit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int32_t* status,
+                                             uint64_t timeout_ns) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vbar = bar;
+    int ok = vbar[2] == 0;
+    if (ok) {
+      unsigned gen = vbar[1];
+      __threadfence();
+      unsigned arrived = atomicAdd(&bar[0], 1u);
+      if (arrived == gridDim.x * gridDim.y - 1) {
+        bar[0] = 0;
+        __threadfence();
+        atomicExch(&bar[1], gen + 1u);
+      } else {
+        uint64_t t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while (vbar[1] == gen) {
+          if (vbar[2] != 0) { ok = 0; break; }
+          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+            set_status(status, CNMF_E_TIMEOUT);
+            atomicExch(&bar[2], 1u);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+struct Carve {
+  // Bump allocator over the caller's workspace (256-byte aligned pieces).
+  char* base;
+  size_t cap;
+  size_t off;
+  __host__ Carve(void* b, size_t c) : base((char*)b), cap(c), off(0) {}
+  template <typename T>
+  __host__ T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += bytes;
+    return p;
+  }
+  __host__ bool fits() const { return off <= cap; }
+};
+
+int num_sms();                       // SM count of the current device
+int max_smem_optin();                // opt-in shared memory per block (bytes)
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) that never leaves a
+// pending error behind; returns false if `bytes` is not allowed.
+bool set_max_smem(const void* func, size_t bytes);
+size_t static_smem(const void* func);  // static shared memory of a kernel
+// Remembers (per host thread) the CUDA error behind the last CNMF_E_CUDA.
+void record_cuda_error(cudaError_t e, const char* file, int line);
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int pad_k(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 48 ? 48 : (k <= 64 ? 64 : (k <= 80 ? 80 : (k <= 96 ? 96 : 128))))); }
+inline size_t wbytes(cnmf_dtype t) { return t == CNMF_F64 ? 8 : 4; }
+
+}  // namespace cnmf
+
+#define CNMF_CHECK_LAUNCH()                                   \
+  do {                                                        \
+    cudaError_t _e = cudaPeekAtLastError();                   \
+    if (_e != cudaSuccess) {                                  \
+      (void)cudaGetLastError();                               \
+      cnmf::record_cuda_error(_e, __FILE__, __LINE__);        \
+      return CNMF_E_CUDA;                                     \
+    }                                                         \
+  } while (0)
+
+// Check a CUDA runtime call that returns cudaError_t.
+#define CNMF_CUDA(call)                                       \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) {                                  \
+      (void)cudaGetLastError();                               \
+      cnmf::record_cuda_error(_e, __FILE__, __LINE__);        \
+      return CNMF_E_CUDA;                                     \
+    }                                                         \
+  } while (0)
+
+#define CNMF_TRY(expr)                  \
+  do {                                  \
+    cnmf_status _s = (expr);            \
+    if (_s != CNMF_OK) return _s;       \
+  } while (0)

@@ -1,0 +1,168 @@
+// Two-sided structured random compression (Alg. 1 applied to A and A^T,
+// Sec. III) and its building blocks, behind the C ABI.
+//
+// Pass t = 0 .. 2q forms one product A . X (n x d -> m x d) and one product
+// A^T . Y (m x d -> n x d).  At even t the A-product belongs to the left
+// chain (L: A Omega, A A^T A Omega, ...) and the A^T-product to the right
+// chain (R^T: A^T Psi, ...); at odd t the roles swap.  Every product is
+// re-orthonormalised (CholeskyQR2) before it feeds the next pass, so after
+// pass 2q the m x d panel is L and the n x d panel is R^T.  One more product
+// gives A-check = A R^T and then A-tilde = L^T A-check (Alg. 4 setup).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cnmf {
+
+static bool valid_type(cnmf_dtype t) {
+  return t == CNMF_F64 || t == CNMF_F32 || t == CNMF_BF16;
+}
+static cnmf_dtype work_type(cnmf_dtype a) {
+  return a == CNMF_F64 ? CNMF_F64 : CNMF_F32;
+}
+
+struct CompressLayout {
+  int KP;
+  size_t bytes;
+  // pieces (null base -> offsets only)
+  void *om, *ps, *m0, *m1, *n0, *n1, *acheck, *prod_ws, *orth_ws;
+  size_t prod_bytes, orth_bytes;
+};
+
+static CompressLayout compress_layout(void* ws, int64_t m, int64_t n, int d,
+                                      cnmf_dtype a_type) {
+  CompressLayout L;
+  cnmf_dtype w = work_type(a_type);
+  size_t e = wbytes(w);
+  L.KP = pad_k(d);
+  Carve cv(ws, SIZE_MAX);
+  L.om = cv.take<char>((size_t)n * d * e);
+  L.ps = cv.take<char>((size_t)m * d * e);
+  L.m0 = cv.take<char>((size_t)m * L.KP * e);
+  L.m1 = cv.take<char>((size_t)m * L.KP * e);
+  L.n0 = cv.take<char>((size_t)n * L.KP * e);
+  L.n1 = cv.take<char>((size_t)n * L.KP * e);
+  L.acheck = cv.take<char>((size_t)m * L.KP * e);
+  L.prod_bytes = prod_workspace(m, n, d, a_type);
+  L.prod_ws = cv.take<char>(L.prod_bytes);
+  L.orth_bytes = std::max(orth_workspace(std::max(m, n), d, w),
+                          cross_workspace(m, d, w));
+  L.orth_ws = cv.take<char>(L.orth_bytes);
+  L.bytes = cv.off;
+  return L;
+}
+
+}  // namespace cnmf
+
+using namespace cnmf;
+
+extern "C" size_t cnmf_sketch_workspace(int64_t m, int64_t n, int32_t k,
+                                        cnmf_dtype a_type) {
+  if (m < 0 || n < 0 || k < 1 || k > 128 || !valid_type(a_type)) return 0;
+  return prod_workspace(m, n, k, a_type);
+}
+
+extern "C" cnmf_status cnmf_sketch_pass(const void* A, cnmf_dtype a_type,
+                                        int64_t m, int64_t n, int64_t lda,
+                                        int32_t k, const void* X, const void* Y,
+                                        void* Zm, void* Zn, void* ws,
+                                        size_t ws_bytes, cnmf_stream_t stream) {
+  if (!valid_type(a_type) || m < 1 || n < 1 || lda < n || k < 1 || k > 128 ||
+      !A || (!X != !Zm) || (!Y != !Zn) || (!X && !Y) || !ws)
+    return CNMF_E_INVALID_ARG;
+  if (ws_bytes < prod_workspace(m, n, k, a_type)) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (X) {
+    ProdArgs pa{A, a_type, m, n, lda, false, X, k, k, Zm, k, k};
+    CNMF_TRY(launch_prod(pa, ws, ws_bytes, s));
+  }
+  if (Y) {
+    ProdArgs pa{A, a_type, m, n, lda, true, Y, k, k, Zn, k, k};
+    CNMF_TRY(launch_prod(pa, ws, ws_bytes, s));
+  }
+  return CNMF_OK;
+}
+
+extern "C" size_t cnmf_orth_workspace(int64_t rows, int32_t k,
+                                      cnmf_dtype w_type) {
+  if (rows < 1 || k < 1 || k > 128 ||
+      (w_type != CNMF_F64 && w_type != CNMF_F32))
+    return 0;
+  return orth_workspace(rows, k, w_type);
+}
+
+extern "C" cnmf_status cnmf_orth(void* Y, cnmf_dtype w_type, int64_t rows,
+                                 int32_t k, void* ws, size_t ws_bytes,
+                                 int32_t* dev_status, cnmf_stream_t stream) {
+  if (!Y || !ws || rows < k || k < 1 || k > 128 ||
+      (w_type != CNMF_F64 && w_type != CNMF_F32))
+    return CNMF_E_INVALID_ARG;
+  if (ws_bytes < orth_workspace(rows, k, w_type)) return CNMF_E_WORKSPACE;
+  OrthPanel p{Y, rows, k, Y, k};
+  return launch_orth(&p, 1, k, w_type, ws, ws_bytes, dev_status,
+                     (cudaStream_t)stream);
+}
+
+extern "C" size_t cnmf_compress_workspace(int64_t m, int64_t n, int32_t d,
+                                          cnmf_dtype a_type) {
+  if (m < 1 || n < 1 || d < 1 || d > 128 || !valid_type(a_type)) return 0;
+  return compress_layout(nullptr, m, n, d, a_type).bytes;
+}
+
+extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
+                                     int64_t m, int64_t n, int64_t lda,
+                                     int32_t r, int32_t d, int32_t q,
+                                     uint64_t seed, const void* Omega,
+                                     const void* Psi, void* L, void* Rt,
+                                     void* Atilde, void* ws, size_t ws_bytes,
+                                     int32_t* dev_status,
+                                     cnmf_stream_t stream) {
+  if (!valid_type(a_type) || !A || !L || !Rt || !Atilde || !ws || m < 1 ||
+      n < 1 || lda < n || r < 1 || d < r || d > 128 || d > m || d > n ||
+      q < 0 || q > 64)
+    return CNMF_E_INVALID_ARG;
+  CompressLayout lay = compress_layout(ws, m, n, d, a_type);
+  if (ws_bytes < lay.bytes) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cnmf_dtype w = work_type(a_type);
+  const int KP = lay.KP;
+
+  const void* X = Omega;   // n x d operand of the A-product
+  int64_t ldx = d;
+  const void* Y = Psi;     // m x d operand of the A^T-product
+  int64_t ldy = d;
+  if (!X) {
+    CNMF_TRY(launch_gaussian(seed, 0, n * (int64_t)d, w, lay.om, s));
+    X = lay.om;
+  }
+  if (!Y) {
+    CNMF_TRY(launch_gaussian(seed, 1, m * (int64_t)d, w, lay.ps, s));
+    Y = lay.ps;
+  }
+  void* mb[2] = {lay.m0, lay.m1};
+  void* nb[2] = {lay.n0, lay.n1};
+  const int T = 2 * q + 1;
+  for (int t = 0; t < T; ++t) {
+    const bool last = (t == T - 1);
+    void* zm = mb[t & 1];
+    void* zn = nb[t & 1];
+    ProdArgs pa{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d};
+    CNMF_TRY(launch_prod(pa, lay.prod_ws, lay.prod_bytes, s));
+    ProdArgs pt{A, a_type, m, n, lda, true, Y, ldy, d, zn, KP, d};
+    CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
+    OrthPanel op[2] = {{zm, m, KP, last ? L : zm, last ? d : KP},
+                       {zn, n, KP, last ? Rt : zn, last ? d : KP}};
+    CNMF_TRY(launch_orth(op, 2, d, w, lay.orth_ws, lay.orth_bytes, dev_status,
+                         s));
+    // next pass: A-product takes the n x d panel, A^T-product the m x d one
+    X = zn; ldx = KP;
+    Y = zm; ldy = KP;
+  }
+  // A-check = A R^T (m x d), then A-tilde = L^T A-check (d x d)
+  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, KP, d};
+  CNMF_TRY(launch_prod(pc, lay.prod_ws, lay.prod_bytes, s));
+  CNMF_TRY(launch_cross(L, d, lay.acheck, KP, m, d, w, Atilde, d, lay.orth_ws,
+                        lay.orth_bytes, s));
+  return CNMF_OK;
+}

@@ -1,0 +1,61 @@
+// Internal launchers shared between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace cnmf {
+
+cnmf_status launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t count,
+                            cnmf_dtype t, void* out, cudaStream_t s);
+
+// ---- products with A (Alg. 1 power scheme) -------------------------------
+// Z (P x kz, pitch ldz) = op(A) B, op(A) = A (P = m, S = n) or A^T (P = n,
+// S = m); B is S x kb (pitch ldb), columns kb..KP-1 read as zero.
+struct ProdArgs {
+  const void* A;
+  cnmf_dtype a_type;
+  int64_t m, n, lda;
+  bool trans;
+  const void* B;
+  int64_t ldb;
+  int kb;
+  void* Z;
+  int64_t ldz;
+  int kz;
+};
+size_t prod_workspace(int64_t m, int64_t n, int k, cnmf_dtype a_type);
+cnmf_status launch_prod(const ProdArgs& a, void* ws, size_t ws_bytes,
+                        cudaStream_t s);
+
+// ---- CholeskyQR2 on up to two tall panels at once --------------------------
+struct OrthPanel {
+  void* Y;       // in: rows x k panel (pitch ld); out: Q (pitch ldo) in Q
+  int64_t rows;
+  int64_t ld;
+  void* Q;       // may equal Y when ldo == ld
+  int64_t ldo;
+};
+size_t orth_workspace(int64_t max_rows, int k, cnmf_dtype w);
+cnmf_status launch_orth(const OrthPanel* p, int npanels, int k, cnmf_dtype w,
+                        void* ws, size_t ws_bytes, int32_t* dev_status,
+                        cudaStream_t s);
+
+// ---- R^-1 (KP x KP, W-typed, KP = pad_k(k)) of the Cholesky factor of
+//      Y^T Y + shift_abs I (FP64-accurate Gram, FP64 Cholesky) -------------
+cnmf_status launch_gram_chol(const void* Y, int64_t ld, int64_t rows, int k,
+                             cnmf_dtype w, double shift_abs, void* rinv_out,
+                             void* ws, size_t ws_bytes, int32_t* status,
+                             cudaStream_t s);
+
+// ---- C (kx x ky, W-typed, pitch ldc) = X^T Y over `rows` rows --------------
+size_t cross_workspace(int64_t rows, int k, cnmf_dtype w);
+cnmf_status launch_cross(const void* X, int64_t ldx, const void* Y,
+                         int64_t ldy, int64_t rows, int k, cnmf_dtype w,
+                         void* C, int64_t ldc, void* ws, size_t ws_bytes,
+                         cudaStream_t s);
+
+// ---- copy a rows x k block between pitches (W-typed) -----------------------
+cnmf_status launch_copy2d(const void* src, int64_t lds, void* dst, int64_t ldd,
+                          int64_t rows, int k, cnmf_dtype w, cudaStream_t s);
+
+}  // namespace cnmf

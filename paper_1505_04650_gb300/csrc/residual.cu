@@ -1,0 +1,157 @@
+// Relative reconstruction error of Sec. V: ||A - U V||_F^2 and ||A||_F^2 in
+// one read of A.  64 x 64 tiles of A; the matching 64 rows of U and of
+// Vt = V^T are staged in shared memory and each thread forms a 4 x 4 block
+// of U V^T (FMA over r), subtracts it from A and accumulates squares (FP32
+// within a tile, FP64 across tiles).  A persistent grid writes one FP64
+// partial pair per CTA; a second launch sums them in CTA order.
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cnmf {
+
+constexpr int RS_NT = 256;
+constexpr int RS_T = 64;
+
+template <typename TA, typename W>
+__global__ void __launch_bounds__(RS_NT)
+    k_residual(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+               const W* __restrict__ U, const W* __restrict__ Vt, int r,
+               double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int RPAD = r + 1;
+  W* Us = reinterpret_cast<W*>(smem);   // 64 x (r+1)
+  W* Vs = Us + RS_T * RPAD;             // 64 x (r+1)
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int64_t tm = ceil_div(m, RS_T), tn = ceil_div(n, RS_T);
+  const int64_t ntiles = tm * tn;
+  double e2 = 0.0, a2 = 0.0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i0 = (t / tn) * RS_T, j0 = (t % tn) * RS_T;
+    __syncthreads();
+    for (int e = threadIdx.x; e < RS_T * r; e += RS_NT) {
+      int i = e / r, b = e % r;
+      Us[i * RPAD + b] = (i0 + i < m) ? U[(i0 + i) * r + b] : W(0);
+      Vs[i * RPAD + b] = (j0 + i < n) ? Vt[(j0 + i) * r + b] : W(0);
+    }
+    __syncthreads();
+    W acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = W(0);
+    for (int l = 0; l < r; ++l) {
+      W uu[4], vv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) uu[a] = Us[(ty + 16 * a) * RPAD + l];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) vv[b] = Vs[(tx + 16 * b) * RPAD + l];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(uu[a], vv[b], acc[a][b]);
+    }
+    W se = W(0), sa = W(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int64_t i = i0 + ty + 16 * a;
+      if (i >= m) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int64_t j = j0 + tx + 16 * b;
+        if (j >= n) continue;
+        W av = widen<W>(A[i * lda + j]);
+        W df = av - acc[a][b];
+        se = fma(df, df, se);
+        sa = fma(av, av, sa);
+      }
+    }
+    e2 += (double)se;
+    a2 += (double)sa;
+  }
+  // block reduction in FP64 (fixed order)
+  __shared__ double re[RS_NT], ra[RS_NT];
+  re[threadIdx.x] = e2;
+  ra[threadIdx.x] = a2;
+  __syncthreads();
+  for (int s = RS_NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      re[threadIdx.x] += re[threadIdx.x + s];
+      ra[threadIdx.x] += ra[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = re[0];
+    part[2 * blockIdx.x + 1] = ra[0];
+  }
+}
+
+__global__ void k_residual_sum(const double* __restrict__ part, int G,
+                               double* __restrict__ out2) {
+  if (threadIdx.x == 0) {
+    double e = 0.0, a = 0.0;
+    for (int g = 0; g < G; ++g) { e += part[2 * g]; a += part[2 * g + 1]; }
+    out2[0] = e;
+    out2[1] = a;
+  }
+}
+
+static int res_grid(int64_t m, int64_t n) {
+  int64_t tiles = ceil_div(m, RS_T) * ceil_div(n, RS_T);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 4 * num_sms()));
+}
+
+template <typename TA, typename W>
+static cnmf_status run_res(const void* A, int64_t m, int64_t n, int64_t lda,
+                           const void* U, const void* Vt, int r, double* out2,
+                           void* ws, cudaStream_t s) {
+  const int G = res_grid(m, n);
+  const size_t smem = sizeof(W) * 2 * RS_T * (r + 1);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    set_max_smem((const void*)k_residual<TA, W>, sizeof(W) * 2 * RS_T * 129);
+  });
+  double* part = (double*)ws;
+  k_residual<TA, W><<<G, RS_NT, smem, s>>>((const TA*)A, m, n, lda,
+                                           (const W*)U, (const W*)Vt, r, part);
+  CNMF_CHECK_LAUNCH();
+  k_residual_sum<<<1, 32, 0, s>>>(part, G, out2);
+  CNMF_CHECK_LAUNCH();
+  return CNMF_OK;
+}
+
+}  // namespace cnmf
+
+using namespace cnmf;
+
+extern "C" size_t cnmf_residual_workspace(int64_t m, int64_t n, int32_t r,
+                                          cnmf_dtype a_type) {
+  (void)r; (void)a_type;
+  if (m < 1 || n < 1) return 0;
+  return (size_t)2 * sizeof(double) * res_grid(m, n) + 256;
+}
+
+extern "C" cnmf_status cnmf_residual(const void* A, cnmf_dtype a_type,
+                                     int64_t m, int64_t n, int64_t lda,
+                                     const void* U, const void* Vt,
+                                     cnmf_dtype w_type, int32_t r,
+                                     double* out2, void* ws, size_t ws_bytes,
+                                     cnmf_stream_t stream) {
+  if (!A || !U || !Vt || !out2 || !ws || m < 1 || n < 1 || lda < n || r < 1 ||
+      r > 128 || (a_type != CNMF_F64 && a_type != CNMF_F32 &&
+                  a_type != CNMF_BF16) ||
+      (w_type != CNMF_F64 && w_type != CNMF_F32) ||
+      (a_type == CNMF_F64) != (w_type == CNMF_F64))
+    return CNMF_E_INVALID_ARG;
+  if (ws_bytes < cnmf_residual_workspace(m, n, r, a_type))
+    return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a_type == CNMF_F64)
+    return run_res<double, double>(A, m, n, lda, U, Vt, r, out2, ws, s);
+  if (a_type == CNMF_F32)
+    return run_res<float, float>(A, m, n, lda, U, Vt, r, out2, ws, s);
+  return run_res<bf16, float>(A, m, n, lda, U, Vt, r, out2, ws, s);
+}

@@ -1,0 +1,43 @@
+"""Helpers for the GPU parity tests: device transfer of seeded inputs and
+tolerance arithmetic.  No method arithmetic lives here."""
+import numpy as np
+import pytest
+
+U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+
+
+def need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_04650_gb300 import build
+    build.build()
+    return torch
+
+
+def to_dev(x: np.ndarray, storage: str):
+    """Storage-form numpy array (see synth.as_storage) -> CUDA tensor."""
+    import torch
+    if storage == "bf16":
+        t = torch.from_numpy(x.view(np.int16).copy()).view(torch.bfloat16)
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(x))
+    return t.cuda()
+
+
+def to_np(t) -> np.ndarray:
+    return t.detach().double().cpu().numpy()
+
+
+def wdt(storage: str):
+    import torch
+    return torch.float64 if storage == "f64" else torch.float32
+
+
+def unit(storage: str) -> float:
+    return U64 if storage == "f64" else U32
+
+
+def rel(a, b) -> float:
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

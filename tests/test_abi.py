@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must load, export every entry point that include/cnmf.h
+declares, and reject invalid arguments on the host with
+CNMF_E_INVALID_ARG before anything is enqueued.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "cnmf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(
+        r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\*?((?:cnmf|snmf)_[a-z0-9_]+)\s*\(",
+        txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1505_04650_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("cnmf_compress", "cnmf_factor", "snmf_select",
+                 "cnmf_residual", "cnmf_status_string", "cnmf_factor_plain"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1505_04650_gb300 import _lib
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, name
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        s = lib.cnmf_status_string(code).decode()
+        assert s.startswith("CNMF_")
+    assert lib.cnmf_status_string(99).decode() == "CNMF_E_UNKNOWN"
+    assert lib.cnmf_abi_version() == 1
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    from paper_1505_04650_gb300._lib import AdmmParams
+    E = 1  # CNMF_E_INVALID_ARG
+    nul = None
+    # NULL A / bad sizes / d > min(m, n) / r > d / q < 0 / lda < n
+    assert lib.cnmf_compress(nul, 1, 10, 10, 10, 2, 4, 1, 0, nul, nul, 1, 1, 1,
+                             1, 1 << 20, nul, nul) == E
+    fake = C.c_void_p(16)
+    assert lib.cnmf_compress(fake, 1, 10, 10, 9, 2, 4, 1, 0, nul, nul, fake,
+                             fake, fake, fake, 1 << 20, nul, nul) == E
+    assert lib.cnmf_compress(fake, 1, 10, 3, 3, 2, 4, 1, 0, nul, nul, fake,
+                             fake, fake, fake, 1 << 20, nul, nul) == E
+    assert lib.cnmf_compress(fake, 1, 10, 10, 10, 5, 4, 1, 0, nul, nul, fake,
+                             fake, fake, fake, 1 << 20, nul, nul) == E
+    assert lib.cnmf_compress(fake, 1, 10, 10, 10, 2, 4, -1, 0, nul, nul, fake,
+                             fake, fake, fake, 1 << 20, nul, nul) == E
+    assert lib.cnmf_compress(fake, 7, 10, 10, 10, 2, 4, 1, 0, nul, nul, fake,
+                             fake, fake, fake, 1 << 20, nul, nul) == E
+    p = AdmmParams(0.0, 1.0, 1.0, 10, 0)      # lambda must be > 0
+    assert lib.cnmf_factor(fake, fake, fake, 1, 10, 10, 2, 4, C.byref(p), fake,
+                           fake, fake, 0, fake, 1 << 20, nul, nul) == E
+    p = AdmmParams(1.0, 1.0, 1.0, 10, 0)
+    assert lib.cnmf_factor(fake, fake, fake, 1, 10, 10, 5, 4, C.byref(p), fake,
+                           fake, fake, 0, fake, 1 << 20, nul, nul) == E
+    assert lib.snmf_select(fake, 1, 10, 10, 10, 3, 2, 1, 0, nul, fake, nul,
+                           fake, 1 << 20, nul, nul) == E
+    assert lib.cnmf_residual(fake, 0, 10, 10, 10, fake, fake, 1, 2, fake,
+                             fake, 1 << 20, nul) == E   # f64 A with f32 U
+    assert lib.cnmf_gaussian(0, 0, -1, 3, 1, fake, nul) == E
+    assert lib.cnmf_sketch_pass(fake, 1, 10, 10, 10, 0, fake, nul, fake, nul,
+                                fake, 1 << 20, nul) == E
+
+
+def test_workspace_queries(lib):
+    assert lib.cnmf_compress_workspace(100, 80, 10, 1) > 0
+    assert lib.cnmf_compress_workspace(100, 80, 200, 1) == 0
+    assert lib.cnmf_factor_state_bytes(100, 80, 5, 10, 1) == \
+        ((100 * 5 + 80 * 5 + 2 * 5 * 10) * 4 + 7) // 8 * 8 + 8
+    assert lib.snmf_select_workspace(100, 80, 10, 2) > 0
+    assert lib.cnmf_plain_state_bytes(100, 80, 5, 0) == \
+        (2 * 100 * 5 + 2 * 80 * 5) * 8 + 8
