@@ -238,6 +238,32 @@ cnmf_status cnmf_residual(const void* A, cnmf_dtype a_type, int64_t m,
                           cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_residual_noalloc: the same result as cnmf_residual, for callers that
+ * cannot allocate device memory -- for example a plugin whose host
+ * application owns every device allocation, code running while another
+ * allocator has reserved all of device memory, or a latency-critical loop
+ * that must not reach cudaMalloc and its implicit device synchronisation.
+ * It takes no workspace and allocates nothing: its scratch (one FP64 pair
+ * per CTA, at most 1024 CTAs) is a 16 KiB static device array inside the
+ * library, which every GPU that loads the library keeps until exit.
+ *   - Arguments as in cnmf_residual, minus ws / ws_bytes.
+ *   - The first call on each device (with that device current) looks up the
+ *     array's device address once; make that first call before any stream
+ *     capture.
+ *   - Returns CNMF_E_WORKSPACE if the launch would need more than 1024 CTAs
+ *     (more than 256 SMs); nothing is enqueued then.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and must be serialised by
+ *     the caller.  Nothing in the array needs to start at zero -- each call
+ *     writes every partial it later reads.
+ * (Library utility; the paper has no counterpart.)
+ * ---------------------------------------------------------------------- */
+cnmf_status cnmf_residual_noalloc(const void* A, cnmf_dtype a_type, int64_t m,
+                                  int64_t n, int64_t lda, const void* U,
+                                  const void* Vt, cnmf_dtype w_type, int32_t r,
+                                  double* out2, cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_barrier_selftest: exercises the bounded grid barrier that the
  * persistent kernels (cnmf_factor) use.  A cooperative grid of `ctas` CTAs
  * (<= SM count) passes `rounds` barriers.  If 0 <= skip < ctas, CTA `skip`

@@ -73,6 +73,9 @@ SIGNATURES = {
     "cnmf_residual": (c_int32, [c_void_p, c_int32, c_int64, c_int64, c_int64,
                                 c_void_p, c_void_p, c_int32, c_int32,
                                 c_void_p, c_void_p, c_size_t, c_void_p]),
+    "cnmf_residual_noalloc": (c_int32, [c_void_p, c_int32, c_int64, c_int64,
+                                        c_int64, c_void_p, c_void_p, c_int32,
+                                        c_int32, c_void_p, c_void_p]),
     "cnmf_barrier_selftest": (c_int32, [c_int32, c_int32, c_int32, c_int32,
                                         c_void_p, c_size_t, c_void_p,
                                         c_void_p, c_void_p]),

@@ -123,9 +123,62 @@ static cnmf_status run_res(const void* A, int64_t m, int64_t n, int64_t lda,
   return CNMF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Scratch for cnmf_residual_noalloc: the per-CTA partial pairs of k_residual
+// live in this file-scope device array instead of a caller workspace.  Every
+// GPU that loads the library holds it (16 KiB) until the process exits.
+// Host code must not pass the symbol itself to a kernel -- on the host it is
+// only a stand-in -- so its device address is looked up once per device.
+// ---------------------------------------------------------------------------
+constexpr int RS_NOALLOC_MAX_CTAS = 1024;
+static __device__ __align__(256) double g_res_scratch[2 * RS_NOALLOC_MAX_CTAS];
+
+static std::mutex g_res_scratch_mu;
+static double* g_res_scratch_dev[64];
+
+// Device address of g_res_scratch on the current device (looked up on the
+// first call made with that device current).
+static cnmf_status res_scratch_address(double** out) {
+  int dev = 0;
+  CNMF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return CNMF_E_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_res_scratch_mu);
+  if (!g_res_scratch_dev[dev]) {
+    void* p = nullptr;
+    CNMF_CUDA(cudaGetSymbolAddress(&p, g_res_scratch));
+    g_res_scratch_dev[dev] = static_cast<double*>(p);
+  }
+  *out = g_res_scratch_dev[dev];
+  return CNMF_OK;
+}
+
 }  // namespace cnmf
 
 using namespace cnmf;
+
+extern "C" cnmf_status cnmf_residual_noalloc(const void* A, cnmf_dtype a_type,
+                                             int64_t m, int64_t n, int64_t lda,
+                                             const void* U, const void* Vt,
+                                             cnmf_dtype w_type, int32_t r,
+                                             double* out2,
+                                             cnmf_stream_t stream) {
+  if (!A || !U || !Vt || !out2 || m < 1 || n < 1 || lda < n || r < 1 ||
+      r > 128 || (a_type != CNMF_F64 && a_type != CNMF_F32 &&
+                  a_type != CNMF_BF16) ||
+      (w_type != CNMF_F64 && w_type != CNMF_F32) ||
+      (a_type == CNMF_F64) != (w_type == CNMF_F64))
+    return CNMF_E_INVALID_ARG;
+  // The grid (one partial pair per CTA) must fit the static scratch.
+  if (res_grid(m, n) > RS_NOALLOC_MAX_CTAS) return CNMF_E_WORKSPACE;
+  double* scratch = nullptr;
+  CNMF_TRY(res_scratch_address(&scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a_type == CNMF_F64)
+    return run_res<double, double>(A, m, n, lda, U, Vt, r, out2, scratch, s);
+  if (a_type == CNMF_F32)
+    return run_res<float, float>(A, m, n, lda, U, Vt, r, out2, scratch, s);
+  return run_res<bf16, float>(A, m, n, lda, U, Vt, r, out2, scratch, s);
+}
 
 extern "C" size_t cnmf_residual_workspace(int64_t m, int64_t n, int32_t r,
                                           cnmf_dtype a_type) {
