@@ -253,6 +253,32 @@ def main(argv=None):
     cn.raise_on_status(st, "bench timed region")
     value = world * 1000.0 / ms
 
+    # ---- phase breakdown (CUDA events, same stream)
+    eb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    eb[0].record(stream)
+    L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st,
+                                    ws=ws_c)
+    eb[1].record(stream)
+    U.copy_(U0)
+    Vt.copy_(Vt0)
+    cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
+    eb[2].record(stream)
+    torch.cuda.synchronize()
+    breakdown = {"compress_ms": eb[0].elapsed_time(eb[1]),
+                 "factor_ms": eb[1].elapsed_time(eb[2]),
+                 "factor_us_per_sweep": 1e3 * eb[1].elapsed_time(eb[2]) / iters}
+    ph = torch.zeros(16, dtype=torch.float64, device=dev)
+    U.copy_(U0)
+    Vt.copy_(Vt0)
+    cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f,
+                   phase_ns=ph)
+    torch.cuda.synchronize()
+    names = ["small_algebra", "row_sweep", "barrier1", "cta_reduce", "barrier2",
+             "s_grams", "s_inv1", "s_xt", "s_grams2", "s_inv2", "s_yt", "s_check",
+             "w_urows", "w_ured", "w_vrows", "w_vred"]
+    breakdown["factor_phase_us_per_sweep"] = {
+        k: float(v) / 1e3 / iters for k, v in zip(names, ph.cpu().tolist())}
+
     # ---- dominant kernel: the products with A (one per side per pass)
     X = torch.randn(n, d, device=dev)
     Y = torch.randn(m, d, device=dev)
@@ -295,6 +321,7 @@ def main(argv=None):
                      "hbm_peak_source": peaks["src"],
                      "ms_per_pass": pass_ms},
         "clocks": clk.summary(),
+        "breakdown": breakdown,
         "gpu_launches": launches_per_step(q) * args.steps,
     }
 

@@ -69,6 +69,18 @@ typedef struct {
   double xi;
   int32_t iters;
   int32_t barrier_timeout_ms; /* 0 -> default (2000 ms) */
+  /* Optional device array of phase_ns_len >= 5 doubles (NULL: off).
+   * cnmf_factor adds the nanoseconds CTA 0 spends per phase, summed over
+   * the sweeps: [0] small r x r algebra, [1] row sweep, [2] first grid
+   * barrier, [3] cross-CTA reduction, [4] second grid barrier; with
+   * phase_ns_len >= 12 also the sub-steps of [0] on the register-tiled
+   * path: [5] Grams, [6] first inverse, [7] Xt, [8] second Grams, [9]
+   * second inverse, [10] Yt, [11] finiteness check, [12] U-row updates,
+   * [13] U-side lane sums, [14] V-row updates, [15] V-side lane sums.
+   * Ignored by cnmf_factor_plain. */
+  double* phase_ns;
+  int32_t phase_ns_len;
+  int32_t reserved;
 } cnmf_admm_params;
 
 /* Human-readable name of a status code (static string, never NULL). */

@@ -222,9 +222,11 @@ def cnmf_factor(L: torch.Tensor, Rt: torch.Tensor, Atilde: torch.Tensor,
                 U: torch.Tensor, Vt: torch.Tensor, lam: float, phi: float,
                 iters: int, xi: float = 1.0, state: FactorState | None = None,
                 status: torch.Tensor | None = None,
-                barrier_timeout_ms: int = 0, ws=None):
+                barrier_timeout_ms: int = 0, ws=None,
+                phase_ns: torch.Tensor | None = None):
     """`iters` sweeps of compressed ADMM (Alg. 4); U (m x r), Vt (n x r)
-    are updated in place.  Returns (U, Vt, state, status)."""
+    are updated in place.  Returns (U, Vt, state, status).  `phase_ns`
+    (optional float64[5] on the device) accumulates per-phase times."""
     m, d = L.shape
     n = Rt.shape[0]
     r = U.shape[1]
@@ -245,7 +247,9 @@ def cnmf_factor(L: torch.Tensor, Rt: torch.Tensor, Atilde: torch.Tensor,
     nb = lb.cnmf_factor_workspace(m, n, r, d, _DT[w])
     if ws is None or ws.numel() < nb:
         ws = _ws(nb, dev)
-    p = AdmmParams(lam, phi, xi, iters, barrier_timeout_ms)
+    p = AdmmParams(lam, phi, xi, iters, barrier_timeout_ms,
+                   None if phase_ns is None else phase_ns.data_ptr(),
+                   0 if phase_ns is None else phase_ns.numel(), 0)
     _check(lb.cnmf_factor(_ptr(L), _ptr(Rt), _ptr(Atilde), _DT[w], m, n, r, d,
                           C.byref(p), _ptr(U), _ptr(Vt), _ptr(state.buf),
                           resume, _ptr(ws), ws.numel(), _ptr(st),
@@ -275,7 +279,7 @@ def cnmf_factor_plain(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,
     nb = lb.cnmf_plain_workspace(m, n, r, _DT[A.dtype])
     if ws is None or ws.numel() < nb:
         ws = _ws(nb, dev)
-    p = AdmmParams(lam, phi, xi, iters, 0)
+    p = AdmmParams(lam, phi, xi, iters, 0, None, 0, 0)
     _check(lb.cnmf_factor_plain(_ptr(A), _DT[A.dtype], m, n, lda, r,
                                 C.byref(p), _ptr(U), _ptr(Vt),
                                 _ptr(state.buf), resume, _ptr(ws), ws.numel(),

@@ -22,7 +22,9 @@ CNMF_F64, CNMF_F32, CNMF_BF16 = 0, 1, 2
 
 class AdmmParams(C.Structure):
     _fields_ = [("lambda_", c_double), ("phi", c_double), ("xi", c_double),
-                ("iters", c_int32), ("barrier_timeout_ms", c_int32)]
+                ("iters", c_int32), ("barrier_timeout_ms", c_int32),
+                ("phase_ns", c_void_p), ("phase_ns_len", c_int32),
+                ("reserved", c_int32)]
 
 
 # name -> (restype, argtypes)

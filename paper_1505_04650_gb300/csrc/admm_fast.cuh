@@ -1,0 +1,425 @@
+// Register-tiled path of the compressed ADMM kernel (Alg. 4) for d <= 64,
+// r <= 32.  Included by admm.cu after the generic path.
+//
+// Layout: every matrix with an r-long dimension is stored with that
+// dimension last and padded to RP = 4 ceil(r / 4) (zeros in the padding),
+// so four consecutive columns are one 16-byte shared-memory load:
+//   At   d x d            Atilde
+//   YtT  d x RP           Yt^T
+//   Xt   d x RP           Xt
+//   M    d x RP           MX (then MY^T)
+//   G    r x RP           Gram matrix, then -(Gram)^-1
+// Shares of the next sweep's SX = L^T (lam U - Lam) and SY^T =
+// R (phi V - Phi)^T (both d x r) are reduced in that layout.
+//
+// One small-algebra step is six block-wide phases:
+//   M  = SX + At Yt^T            G = Yt Yt^T + lam I        (one phase)
+//   G <- -G^-1                                              (sweep operator)
+//   Xt = M (Yt Yt^T + lam I)^-1
+//   M  = SY^T + At^T Xt          G = Xt^T Xt + phi I        (one phase)
+//   G <- -G^-1
+//   Yt^T = M (Xt^T Xt + phi I)^-1    (= (G^-1 MY)^T, G symmetric)
+// Each output quad C[p][4q..4q+3] is one thread's task: a length-S loop of
+// one scalar load, one 16-byte load and four FMAs.
+
+struct FastSmem {
+  int RP, dp, nl;
+  int At, YtT, Xt, M, G, v, Red, sL, sU, sLam, sRt, sVt, sPhit, total;
+  // dmax: the register tile width; resident rows are stored zero-padded to
+  // dmax with pitch dmax + 4 (4 banks apart: the <= 8 rows one warp reads
+  // with 16-byte loads hit distinct banks).
+  __host__ __device__ FastSmem(int r, int d, bool res, int64_t mu,
+                               int64_t nv, int dmax) {
+    RP = (r + 3) & ~3;
+    dp = dmax + 4;
+    nl = AD_NT / r;
+    int o = 0;
+    auto take = [&](int64_t n) { int p = o; o += (int)((n + 3) & ~3); return p; };
+    At = take(d * d);
+    YtT = take(d * RP);
+    Xt = take(d * RP);
+    M = take(d * RP);
+    G = take(r * RP);
+    v = take(2 * 32);
+    Red = take((int64_t)nl * d * r);
+    sL = res ? take(mu * dp) : 0;
+    sU = res ? take(mu * r) : 0;
+    sLam = res ? take(mu * r) : 0;
+    sRt = res ? take(nv * dp) : 0;
+    sVt = res ? take(nv * r) : 0;
+    sPhit = res ? take(nv * r) : 0;
+    total = o;
+  }
+};
+
+// C[p][4q..4q+3] = init + scale * sum_{s < S} A(p, s) B[s][4q..4q+3]
+// for all tasks (p, q), p < P, q < RP/4; A(p, s) = A[p * sap + s * sas].
+template <typename W>
+__device__ __forceinline__ void quad_mm(W* C, int RP, const W* A, int sap,
+                                        int sas, const W* B, int P, int S,
+                                        W scale, const W* init_g, int init_ld,
+                                        int init_cols, W diag, int task0,
+                                        int ntask_total) {
+  const int Q = RP / 4;
+  for (int t = threadIdx.x - task0; t < P * Q; t += AD_NT) {
+    if (t < 0) continue;
+    const int p = t / Q, q = t % Q;
+    W c0 = W(0), c1 = W(0), c2 = W(0), c3 = W(0);
+    W ini[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = 4 * q + j;
+      ini[j] = (init_g && col < init_cols) ? __ldcg(init_g + p * init_ld + col)
+                                           : W(0);
+    }
+    const W* ap = A + p * sap;
+    const W* bp = B + 4 * q;
+#pragma unroll 4
+    for (int s = 0; s < S; ++s) {
+      const W av = ap[s * sas];
+      W b4[4];
+      ldsN<4, W>(bp + s * RP, b4);
+      c0 = fma(av, b4[0], c0);
+      c1 = fma(av, b4[1], c1);
+      c2 = fma(av, b4[2], c2);
+      c3 = fma(av, b4[3], c3);
+    }
+    W o[4] = {c0 * scale, c1 * scale, c2 * scale, c3 * scale};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = 4 * q + j;
+      o[j] += ini[j];
+      if (col == p) o[j] += diag;
+      if (col >= init_cols) o[j] = W(0);   // keep the padding at zero
+      C[p * RP + col] = o[j];
+    }
+  }
+  (void)ntask_total;
+}
+
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+// -G^-1 in place for the leading r x r block of G (pitch RP <= RMAX): the
+// sweep operator of spd_sweep_inverse with every entry quad held in a
+// register of one thread for all pivots (thread (i, q) owns G[i][4q..4q+3]);
+// the pivot column is published through a double-buffered shared vector, so
+// each pivot costs one block barrier.  Rows/columns beyond r hold the
+// identity and are never pivoted.
+template <typename W, int RMAX>
+__device__ void fast_sweep_inverse(W* G, W* vbuf, int r, int RP,
+                                   int32_t* status) {
+  constexpr int QM = RMAX / 4;
+  const int t = threadIdx.x;
+  const bool own = t < RMAX * QM;
+  const int i = t / QM, q = t % QM;
+  W g[4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int k = 4 * q + jj;
+    g[jj] = (own && i < r && k < r) ? G[i * RP + k] : (i == k ? W(1) : W(0));
+  }
+  for (int j = 0; j < r; ++j) {
+    W* v = vbuf + (j & 1) * 32;
+    if (own && q == (j >> 2)) {
+      const int jj = j & 3;
+      v[i] = jj == 0 ? g[0] : (jj == 1 ? g[1] : (jj == 2 ? g[2] : g[3]));
+    }
+    __syncthreads();
+    W dj = v[j];
+    if (!(dj > W(0))) {
+      if (t == 0)
+        set_status(status, isfinite((double)dj) ? CNMF_E_CHOLESKY
+                                                : CNMF_E_NONFINITE);
+      dj = W(1);
+    }
+    const W id = fast_rcp(dj);
+    if (own) {
+      const W vi = v[i];
+      const W vid = vi * id;
+      W vk[4];
+      ldsN<4, W>(v + 4 * q, vk);
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int k = 4 * q + jj;
+        const W gen = fma(-vid, vk[jj], g[jj]);
+        g[jj] = (i == j) ? ((k == j) ? -id : vk[jj] * id)
+                         : ((k == j) ? vid : gen);
+      }
+    }
+  }
+  __syncthreads();
+  if (own && i < r) {
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int k = 4 * q + jj;
+      if (k < RP) G[i * RP + k] = (k < r) ? g[jj] : W(0);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename W, int RMAX>
+__device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
+                           uint64_t* sub = nullptr) {
+  const int r = a.r, d = a.d, RP = o.RP, Q = RP / 4;
+  uint64_t tm = sub ? globaltimer_ns() : 0;
+  auto mark = [&](int i) {
+    if (sub) { uint64_t t = globaltimer_ns(); sub[i] += t - tm; tm = t; }
+  };
+  W* At = sm + o.At;
+  W* YtT = sm + o.YtT;
+  W* Xt = sm + o.Xt;
+  W* M = sm + o.M;
+  W* G = sm + o.G;
+  // M = SX + At Yt^T  (d x RP);  G = Yt Yt^T + lam I  (r x RP)
+  quad_mm<W>(M, RP, At, d, 1, YtT, d, d, W(1), a.SX, r, r, W(0), 0, 0);
+  quad_mm<W>(G, RP, YtT, 1, RP, YtT, r, d, W(1), nullptr, 0, r, a.lam,
+             d * Q, 0);
+  __syncthreads();
+  mark(0);
+  fast_sweep_inverse<W, RMAX>(G, sm + o.v, r, RP, a.status);
+  mark(1);
+  // Xt = M (Yt Yt^T + lam I)^-1 = -M G
+  quad_mm<W>(Xt, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, 0);
+  __syncthreads();
+  mark(2);
+  // M = SY^T + At^T Xt (d x RP);  G = Xt^T Xt + phi I
+  quad_mm<W>(M, RP, At, 1, d, Xt, d, d, W(1), a.SY, r, r, W(0), 0, 0);
+  quad_mm<W>(G, RP, Xt, 1, RP, Xt, r, d, W(1), nullptr, 0, r, a.phi,
+             d * Q, 0);
+  __syncthreads();
+  mark(3);
+  fast_sweep_inverse<W, RMAX>(G, sm + o.v, r, RP, a.status);
+  mark(4);
+  // Yt^T = M (Xt^T Xt + phi I)^-1 = -M G
+  quad_mm<W>(YtT, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, 0);
+  __syncthreads();
+  mark(5);
+  for (int e = threadIdx.x; e < d * r; e += AD_NT) {
+    const W y = YtT[(e / r) * RP + e % r];
+    if (!isfinite(y)) set_status(a.status, CNMF_E_NONFINITE);
+  }
+  mark(6);
+}
+
+// Thread (l, b): column b of Xt (U side) or Yt^T (V side) in registers;
+// rows l, l + nl, ... of this CTA; shares accumulated in registers and
+// added over lanes in lane order.  mode 0: fresh setup (Lam = Phi = 0,
+// shares of lam U and phi V, plus Yt0^T = R V^T); mode 1: resume setup;
+// mode 2: ADMM row updates.
+template <typename W, int DMAX, bool RES>
+__device__ void sweep_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
+                           int mode, uint64_t* sub = nullptr) {
+  uint64_t tm = sub ? globaltimer_ns() : 0;
+  auto mark = [&](int i) {
+    if (sub) { uint64_t t = globaltimer_ns(); sub[i] += t - tm; tm = t; }
+  };
+  const int r = a.r, d = a.d, dp = o.dp, RP = o.RP, nl = o.nl;
+  const int64_t G = gridDim.x, c = blockIdx.x;
+  const int b = threadIdx.x % r, lr = threadIdx.x / r;
+  const bool active = lr < nl;
+  const int dr = d * r;
+  W* Red = sm + o.Red;
+  W* dst = a.part + (size_t)c * (3 * dr);
+  for (int side = 0; side < 2 + (mode == 0 ? 1 : 0); ++side) {
+    const bool vside = side > 0;
+    const int64_t tot = vside ? a.n : a.m;
+    const int64_t i0 = (c * tot) / G, i1 = ((c + 1) * tot) / G;
+    const W* rows = RES ? sm + (vside ? o.sRt : o.sL) : (vside ? a.Rt : a.L);
+    const int64_t rstride = RES ? dp : d;
+    W* P = RES ? sm + (vside ? o.sVt : o.sU) : (vside ? a.Vt : a.U);
+    W* Qm = RES ? sm + (vside ? o.sPhit : o.sLam) : (vside ? a.Phit : a.Lam);
+    const int64_t pbase = RES ? 0 : i0;
+    const W pen = vside ? a.phi : a.lam;
+    const W ipen = W(1) / pen;
+    const W step = a.xi * pen;
+    const W* coefsrc = sm + (vside ? o.YtT : o.Xt);
+    W coef[DMAX], acc[DMAX];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) {
+      acc[k] = W(0);
+      coef[k] = (mode == 2 && k < d) ? coefsrc[k * RP + b] : W(0);
+    }
+    if (active) {
+      for (int64_t i = i0 + lr; i < i1; i += nl) {
+        const W* row = rows + (i - i0 + (RES ? 0 : i0)) * rstride;
+        const int64_t g = (i - i0 + pbase) * r + b;
+        W x[DMAX];
+        if constexpr (RES) {
+#pragma unroll
+          for (int k = 0; k < DMAX; k += 4) ldsN<4, W>(row + k, x + k);
+        } else {
+#pragma unroll
+          for (int k = 0; k < DMAX; ++k) x[k] = k < d ? row[k] : W(0);
+        }
+        W w;
+        if (side == 2) {
+          w = P[g];                                  // Yt0^T = R V^T
+        } else if (mode == 2) {
+          W t4[4] = {W(0), W(0), W(0), W(0)};
+#pragma unroll
+          for (int k = 0; k < DMAX; ++k) t4[k & 3] = fma(x[k], coef[k], t4[k & 3]);
+          const W t = (t4[0] + t4[1]) + (t4[2] + t4[3]);
+          const W qo = Qm[g];
+          W u = fma(qo, ipen, t);
+          u = u > W(0) ? u : W(0);
+          const W qn = fma(step, t - u, qo);
+          P[g] = u;
+          Qm[g] = qn;
+          w = fma_rn<W>(pen, u, -qn);
+        } else if (mode == 0) {
+          Qm[g] = W(0);
+          w = fma_rn<W>(pen, P[g], -W(0));
+        } else {
+          w = fma_rn<W>(pen, P[g], -Qm[g]);
+        }
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) acc[k] = fma(x[k], w, acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k)
+        if (k < d) Red[lr * dr + k * r + b] = acc[k];
+    }
+    __syncthreads();
+    if (side < 2) mark(2 * side);
+    // lane sums in lane order; the loads are issued before the adds
+    for (int e = threadIdx.x; e < dr; e += AD_NT) {
+      W v[AD_NT / 4];   // nl <= AD_NT / r; r >= 4 keeps this in bounds
+      W t = W(0);
+      int l = 0;
+      for (; l + 8 <= nl; l += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = Red[(l + u) * dr + e];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t += v[u];
+      }
+      for (; l < nl; ++l) t += Red[l * dr + e];
+      dst[side * dr + e] = t;
+    }
+    __syncthreads();
+    if (side < 2) mark(2 * side + 1);
+  }
+}
+
+template <typename W>
+__device__ void fast_resident_copy(const AdmmArgs<W>& a, W* sm,
+                                   const FastSmem& o, int dir) {
+  const int r = a.r, d = a.d, dp = o.dp;  // rows padded with zeros to dp
+  const int64_t G = gridDim.x, c = blockIdx.x;
+  for (int side = 0; side < 2; ++side) {
+    const int64_t tot = side ? a.n : a.m;
+    const int64_t i0 = (c * tot) / G, i1 = ((c + 1) * tot) / G;
+    const int64_t nr = i1 - i0;
+    W* rs = sm + (side ? o.sRt : o.sL);
+    const W* rg = side ? a.Rt : a.L;
+    W* ps = sm + (side ? o.sVt : o.sU);
+    W* pg = side ? a.Vt : a.U;
+    W* qs = sm + (side ? o.sPhit : o.sLam);
+    W* qg = side ? a.Phit : a.Lam;
+    if (dir == 0) {
+      for (int64_t e = threadIdx.x; e < nr * dp; e += AD_NT) {
+        const int64_t ii = e / dp;
+        const int k = (int)(e % dp);
+        rs[e] = k < d ? rg[(i0 + ii) * d + k] : W(0);
+      }
+      for (int64_t e = threadIdx.x; e < nr * r; e += AD_NT) {
+        ps[e] = pg[i0 * r + e];
+        qs[e] = qg[i0 * r + e];
+      }
+    } else {
+      for (int64_t e = threadIdx.x; e < nr * r; e += AD_NT) {
+        pg[i0 * r + e] = ps[e];
+        qg[i0 * r + e] = qs[e];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Cross-CTA sums (one warp per entry, fixed order).  Entries: SX (d x r),
+// SY^T (d x r) and, on a fresh start, Yt0^T (d x r), which is stored to the
+// state as Yt (r x d).
+template <typename W>
+__device__ void reduce_fast(const AdmmArgs<W>& a, int with_y0) {
+  const int dr = a.d * a.r;
+  const int E = 2 * dr + (with_y0 ? dr : 0);
+  const int64_t G = gridDim.x, c = blockIdx.x;
+  const int e0 = (int)((c * E) / G), e1 = (int)(((c + 1) * E) / G);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  for (int e = e0 + warp; e < e1; e += AD_NT / 32) {
+    W s = W(0);
+    const W* p = a.part + e;
+#pragma unroll 4
+    for (int64_t g = lane; g < G; g += 32) s += __ldcg(p + (size_t)g * 3 * dr);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (e < dr) a.SX[e] = s;
+      else if (e < 2 * dr) a.SY[e - dr] = s;
+      else {
+        const int k = (e - 2 * dr) / a.r, bb = (e - 2 * dr) % a.r;
+        a.Yt[bb * a.d + k] = s;
+      }
+    }
+  }
+}
+
+template <typename W, int DMAX, int RMAX, bool RES>
+__global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* sm = reinterpret_cast<W*>(smem_raw);
+  const FastSmem o(a.r, a.d, RES, a.mu, a.nv, DMAX);
+  const int r = a.r, d = a.d, RP = o.RP;
+  const bool prof = a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0;
+  uint64_t tph[5] = {0, 0, 0, 0, 0};
+  uint64_t tsub[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int e = threadIdx.x; e < d * d; e += AD_NT) sm[o.At + e] = a.At[e];
+  for (int e = threadIdx.x; e < d * RP; e += AD_NT) {
+    sm[o.YtT + e] = W(0);
+    sm[o.Xt + e] = W(0);
+  }
+  if (RES) fast_resident_copy<W>(a, sm, o, 0);
+  __syncthreads();
+
+  sweep_fast<W, DMAX, RES>(a, sm, o, a.resume ? 1 : 0);
+  if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
+  reduce_fast<W>(a, a.resume ? 0 : 1);
+  if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
+  for (int e = threadIdx.x; e < d * r; e += AD_NT) {
+    const int k = e / r, bb = e % r;
+    sm[o.YtT + k * RP + bb] = __ldcg(a.Yt + bb * d + k);
+  }
+  __syncthreads();
+  for (int it = 0; it < a.iters; ++it) {
+    uint64_t t0 = prof ? globaltimer_ns() : 0;
+    small_fast<W, RMAX>(a, sm, o, prof ? tsub : nullptr);
+    uint64_t t1 = prof ? globaltimer_ns() : 0;
+    sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 7 : nullptr);
+    uint64_t t2 = prof ? globaltimer_ns() : 0;
+    if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
+    uint64_t t3 = prof ? globaltimer_ns() : 0;
+    reduce_fast<W>(a, 0);
+    uint64_t t4 = prof ? globaltimer_ns() : 0;
+    if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
+    if (prof) {
+      uint64_t t5 = globaltimer_ns();
+      tph[0] += t1 - t0; tph[1] += t2 - t1; tph[2] += t3 - t2;
+      tph[3] += t4 - t3; tph[4] += t5 - t4;
+    }
+  }
+  if (RES) fast_resident_copy<W>(a, sm, o, 1);
+  if (blockIdx.x == 0) {
+    for (int e = threadIdx.x; e < d * r; e += AD_NT) {
+      const int k = e / r, bb = e % r;
+      a.Yt[bb * d + k] = sm[o.YtT + k * RP + bb];
+      if (a.iters > 0) a.Xt[e] = sm[o.Xt + k * RP + bb];
+    }
+    if (threadIdx.x == 0) *a.kcount += a.iters;
+  }
+  if (prof) {
+    for (int i = 0; i < 5; ++i) a.phase_ns[i] += (double)tph[i];
+    const int ns = a.phase_ns_len - 5 < 11 ? a.phase_ns_len - 5 : 11;
+    for (int i = 0; i < ns; ++i) a.phase_ns[5 + i] += (double)tsub[i];
+  }
+}

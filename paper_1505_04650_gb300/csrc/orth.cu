@@ -24,6 +24,7 @@ namespace cnmf {
 
 constexpr int OR_NT = 256;
 constexpr int OR_ROWS = 32;  // rows staged per block
+constexpr int FIN_E = 32;    // Gram entries reduced per k_finish CTA
 
 template <typename W>
 struct GAcc;
@@ -160,18 +161,32 @@ __global__ void __launch_bounds__(OR_NT)
              double shift_rel, double shift_abs, double* __restrict__ gfull,
              W* __restrict__ out0, W* __restrict__ out1, int64_t ldc,
              unsigned* __restrict__ tickets, int32_t* status) {
+  // Each CTA sums FIN_E entries; FIN_S threads per entry split the CTAs
+  // (thread j takes partials j, j + FIN_S, ...), then one thread adds the
+  // FIN_S sub-sums in order -- a fixed order, so the result is deterministic.
+  constexpr int FIN_S = OR_NT / FIN_E;
+  __shared__ double red[FIN_E][FIN_S + 1];
   const int p = blockIdx.y;
-  const int e = blockIdx.x * OR_NT + threadIdx.x;
+  const int le = threadIdx.x / FIN_S, sub = threadIdx.x % FIN_S;
+  const int e = blockIdx.x * FIN_E + le;
   const int a = e / KP, b = e % KP;
   W* out = p ? out1 : out0;
-  if (e < KP * KP && (mode == 0 || a <= b)) {
-    double s = 0.0;
-    if (a < k && b < k)
-      for (int64_t c = 0; c < G; ++c) s += part[((size_t)p * G + c) * KP * KP + e];
+  const bool want = e < KP * KP && (mode == 0 || a <= b) && a < k && b < k;
+  double s = 0.0;
+  if (want) {
+    const double* src = part + (size_t)p * G * KP * KP + e;
+#pragma unroll 4
+    for (int64_t c = sub; c < G; c += FIN_S) s += src[(size_t)c * KP * KP];
+  }
+  red[le][sub] = s;
+  __syncthreads();
+  if (sub == 0 && e < KP * KP && (mode == 0 || a <= b)) {
+    double t = 0.0;
+    for (int j = 0; j < FIN_S; ++j) t += red[le][j];
     if (mode == 0) {
-      if (a < k && b < k) out[a * ldc + b] = (W)s;
+      if (a < k && b < k) out[a * ldc + b] = (W)t;
     } else {
-      gfull[(size_t)p * KP * KP + e] = s;
+      gfull[(size_t)p * KP * KP + e] = want ? t : 0.0;
     }
   }
   if (mode == 0) return;
@@ -304,7 +319,7 @@ static int orth_kp(int k) { return pad_k(k); }
 
 template <typename W>
 static int gram_grid(int64_t rows) {
-  int64_t g = std::max<int64_t>(1, std::min<int64_t>(2 * num_sms(), ceil_div(rows, 64)));
+  int64_t g = std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(rows, 128)));
   return (int)g;
 }
 
@@ -357,7 +372,7 @@ static cnmf_status run_orth(const OrthPanel* pp, int np, int k, void* ws,
     d[i] = PanelDesc{o.Y, o.Y, o.ld, o.ld, o.rows};
   }
   dim3 grid(G, np);
-  const int nfin = (int)ceil_div((int64_t)KP * KP, OR_NT);
+  const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
   const size_t fin_smem = sizeof(double) * KP * KP;
   const size_t ap_smem = sizeof(W) * (KP * KP + 2 * OR_ROWS * (KP + 4));
   const double shift = sizeof(W) == 8 ? 1e-13 : 1e-11;
@@ -396,7 +411,7 @@ static cnmf_status run_cross(const void* X, int64_t ldx, const void* Y,
                          sizeof(W) * 2 * OR_ROWS * (KP + 4), s>>>(d, d, k,
                                                                   part);
   CNMF_CHECK_LAUNCH();
-  const int nfin = (int)ceil_div((int64_t)KP * KP, OR_NT);
+  const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
   k_finish<W, KP><<<dim3(nfin, 1), OR_NT, 0, s>>>(
       part, G, k, 0, 0.0, 0.0, nullptr, (W*)C, (W*)C, ldc, nullptr, nullptr);
   CNMF_CHECK_LAUNCH();
@@ -419,7 +434,7 @@ static cnmf_status run_gram_chol(const void* Y, int64_t ld, int64_t rows,
   k_gram<W, KP, true><<<dim3(G, 1), OR_NT, sizeof(W) * OR_ROWS * (KP + 4), s>>>(
       d, d, k, part);
   CNMF_CHECK_LAUNCH();
-  const int nfin = (int)ceil_div((int64_t)KP * KP, OR_NT);
+  const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
   const size_t fin_smem = sizeof(double) * KP * KP;
   k_finish<W, KP><<<dim3(nfin, 1), OR_NT, fin_smem, s>>>(
       part, G, k, 1, 0.0, shift_abs, gfull, (W*)rinv_out, (W*)rinv_out, 0,

@@ -210,26 +210,40 @@ __global__ void __launch_bounds__(SK_NT)
   }
 }
 
-// Sum the per-CTA partials of split output tiles, in CTA order.
+// Sum the per-CTA partials of split output tiles, in CTA order.  The
+// contributing CTAs of the tile and their partial slots are worked out once
+// per CTA (64-bit integer divisions) and kept in shared memory.
+constexpr int FIX_MAX = 1024;
+
 template <typename W, int KP>
 __global__ void k_prod_fixup(W* __restrict__ Z, int64_t ldz, int kz, int64_t P,
                              const W* __restrict__ part, int64_t U,
                              int64_t chunks, int64_t G) {
+  __shared__ int64_t off[FIX_MAX];
+  __shared__ int nc_s;
   const int64_t tp = blockIdx.x;
   const int64_t ua = tp * chunks, ub = ua + chunks - 1;
   const int64_t ca = split_owner(ua, U, G), cb = split_owner(ub, U, G);
-  if (ca == cb && split_start(ca, U, G) <= ua &&
-      split_start(ca + 1, U, G) > ub)
-    return;  // whole tile written directly by one CTA
+  if (ca == cb) return;  // whole tile written directly by one CTA
+  const int nc = (int)(cb - ca + 1);
+  for (int j = threadIdx.x; j < nc && j < FIX_MAX; j += blockDim.x) {
+    const int64_t c = ca + j;
+    const int slot = (split_start(c, U, G) / chunks == tp) ? 0 : 1;
+    off[j] = ((int64_t)c * 2 + slot) * SK_BP * KP;
+  }
+  if (threadIdx.x == 0) nc_s = nc;
+  __syncthreads();
   const int64_t p0 = tp * SK_BP;
   for (int e = threadIdx.x; e < SK_BP * KP; e += blockDim.x) {
     int lp = e / KP, col = e % KP;
     if (p0 + lp >= P || col >= kz) continue;
     W s = W(0);
-    for (int64_t c = ca; c <= cb; ++c) {
-      int64_t first_u = split_start(c, U, G);
-      int slot = (first_u / chunks == tp) ? 0 : 1;
-      s += part[((size_t)c * 2 + slot) * SK_BP * KP + e];
+    int j = 0;
+    for (; j < nc_s && j < FIX_MAX; ++j) s += part[off[j] + e];
+    for (; j < nc_s; ++j) {  // more contributors than the cache holds
+      const int64_t c = ca + j;
+      const int slot = (split_start(c, U, G) / chunks == tp) ? 0 : 1;
+      s += part[((int64_t)c * 2 + slot) * SK_BP * KP + e];
     }
     Z[(p0 + lp) * ldz + col] = s;
   }

@@ -68,10 +68,10 @@ def test_invalid_arguments_rejected_on_host(lib):
                              fake, fake, fake, 1 << 20, nul, nul) == E
     assert lib.cnmf_compress(fake, 7, 10, 10, 10, 2, 4, 1, 0, nul, nul, fake,
                              fake, fake, fake, 1 << 20, nul, nul) == E
-    p = AdmmParams(0.0, 1.0, 1.0, 10, 0)      # lambda must be > 0
+    p = AdmmParams(0.0, 1.0, 1.0, 10, 0, None, 0, 0)      # lambda must be > 0
     assert lib.cnmf_factor(fake, fake, fake, 1, 10, 10, 2, 4, C.byref(p), fake,
                            fake, fake, 0, fake, 1 << 20, nul, nul) == E
-    p = AdmmParams(1.0, 1.0, 1.0, 10, 0)
+    p = AdmmParams(1.0, 1.0, 1.0, 10, 0, None, 0, 0)
     assert lib.cnmf_factor(fake, fake, fake, 1, 10, 10, 5, 4, C.byref(p), fake,
                            fake, fake, 0, fake, 1 << 20, nul, nul) == E
     assert lib.snmf_select(fake, 1, 10, 10, 10, 3, 2, 1, 0, nul, fake, nul,
