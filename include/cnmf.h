@@ -122,13 +122,20 @@ cnmf_status cnmf_philox_words(uint64_t seed, uint32_t stream_id,
  *   Zn = A^T Y (n x k, from Y m x k),
  * reading A once per product.  X, Y, Zm, Zn are W-typed with row pitch k.
  * Pass X = NULL / Zm = NULL (or Y = NULL / Zn = NULL) to skip one side.
- * 1 <= k <= 128. */
+ * 1 <= k <= 128.  FP64 / FP32 A: CUDA-core FMA, exact products rounded in
+ * W.  BF16 A (16-byte aligned, lda a multiple of 8): tensor cores
+ * (tcgen05, FP32 accumulate) with X / Y split into bf16 hi + lo parts, so
+ * the products carry an extra relative error of at most 2^-18 of |A||X|;
+ * setting the environment variable CNMF_NO_TENSOR_CORES selects the
+ * CUDA-core kernel instead.  dev_status (optional): CNMF_E_TIMEOUT if a
+ * bounded pipeline wait expired. */
 size_t cnmf_sketch_workspace(int64_t m, int64_t n, int32_t k,
                              cnmf_dtype a_type);
 cnmf_status cnmf_sketch_pass(const void* A, cnmf_dtype a_type, int64_t m,
                              int64_t n, int64_t lda, int32_t k, const void* X,
                              const void* Y, void* Zm, void* Zn, void* ws,
-                             size_t ws_bytes, cnmf_stream_t stream);
+                             size_t ws_bytes, int32_t* dev_status,
+                             cnmf_stream_t stream);
 
 /* Orthonormal basis (Alg. 1, last step: "QR decomposition") of a tall
  * panel Y (rows x k, W-typed, row pitch k, rows >= k), in place:

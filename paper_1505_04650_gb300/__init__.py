@@ -124,7 +124,8 @@ def cnmf_philox_words(seed: int, stream_id: int, first_block: int,
 
 
 def cnmf_sketch_pass(A: torch.Tensor, X: torch.Tensor | None = None,
-                     Y: torch.Tensor | None = None):
+                     Y: torch.Tensor | None = None,
+                     status: torch.Tensor | None = None):
     """(A X, A^T Y) with one read of A per product; either may be None."""
     m, n, lda = _mat(A)
     w = _wdtype(A.dtype)
@@ -140,7 +141,8 @@ def cnmf_sketch_pass(A: torch.Tensor, X: torch.Tensor | None = None,
     ws = _ws(nb, A.device)
     _check(L.cnmf_sketch_pass(_ptr(A), _DT[A.dtype], m, n, lda, k, _ptr(X),
                               _ptr(Y), _ptr(Zm), _ptr(Zn), _ptr(ws), nb,
-                              _stream(A.device)), "cnmf_sketch_pass")
+                              _ptr(status), _stream(A.device)),
+           "cnmf_sketch_pass")
     return Zm, Zn
 
 

@@ -40,7 +40,7 @@ SIGNATURES = {
     "cnmf_sketch_pass": (c_int32, [c_void_p, c_int32, c_int64, c_int64,
                                    c_int64, c_int32, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_size_t,
-                                   c_void_p]),
+                                   c_void_p, c_void_p]),
     "cnmf_orth_workspace": (c_size_t, [c_int64, c_int32, c_int32]),
     "cnmf_orth": (c_int32, [c_void_p, c_int32, c_int64, c_int32, c_void_p,
                             c_size_t, c_void_p, c_void_p]),

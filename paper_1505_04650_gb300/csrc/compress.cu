@@ -67,18 +67,19 @@ extern "C" cnmf_status cnmf_sketch_pass(const void* A, cnmf_dtype a_type,
                                         int64_t m, int64_t n, int64_t lda,
                                         int32_t k, const void* X, const void* Y,
                                         void* Zm, void* Zn, void* ws,
-                                        size_t ws_bytes, cnmf_stream_t stream) {
+                                        size_t ws_bytes, int32_t* dev_status,
+                                        cnmf_stream_t stream) {
   if (!valid_type(a_type) || m < 1 || n < 1 || lda < n || k < 1 || k > 128 ||
       !A || (!X != !Zm) || (!Y != !Zn) || (!X && !Y) || !ws)
     return CNMF_E_INVALID_ARG;
   if (ws_bytes < prod_workspace(m, n, k, a_type)) return CNMF_E_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   if (X) {
-    ProdArgs pa{A, a_type, m, n, lda, false, X, k, k, Zm, k, k};
+    ProdArgs pa{A, a_type, m, n, lda, false, X, k, k, Zm, k, k, dev_status};
     CNMF_TRY(launch_prod(pa, ws, ws_bytes, s));
   }
   if (Y) {
-    ProdArgs pa{A, a_type, m, n, lda, true, Y, k, k, Zn, k, k};
+    ProdArgs pa{A, a_type, m, n, lda, true, Y, k, k, Zn, k, k, dev_status};
     CNMF_TRY(launch_prod(pa, ws, ws_bytes, s));
   }
   return CNMF_OK;
@@ -147,9 +148,9 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
     const bool last = (t == T - 1);
     void* zm = mb[t & 1];
     void* zn = nb[t & 1];
-    ProdArgs pa{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d};
+    ProdArgs pa{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d, dev_status};
     CNMF_TRY(launch_prod(pa, lay.prod_ws, lay.prod_bytes, s));
-    ProdArgs pt{A, a_type, m, n, lda, true, Y, ldy, d, zn, KP, d};
+    ProdArgs pt{A, a_type, m, n, lda, true, Y, ldy, d, zn, KP, d, dev_status};
     CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
     OrthPanel op[2] = {{zm, m, KP, last ? L : zm, last ? d : KP},
                        {zn, n, KP, last ? Rt : zn, last ? d : KP}};
@@ -160,7 +161,7 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
     Y = zm; ldy = KP;
   }
   // A-check = A R^T (m x d), then A-tilde = L^T A-check (d x d)
-  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, KP, d};
+  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, KP, d, dev_status};
   CNMF_TRY(launch_prod(pc, lay.prod_ws, lay.prod_bytes, s));
   CNMF_TRY(launch_cross(L, d, lay.acheck, KP, m, d, w, Atilde, d, lay.orth_ws,
                         lay.orth_bytes, s));

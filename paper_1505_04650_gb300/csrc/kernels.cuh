@@ -22,10 +22,21 @@ struct ProdArgs {
   void* Z;
   int64_t ldz;
   int kz;
+  int32_t* status = nullptr;   // device status word (tensor-core path waits)
 };
 size_t prod_workspace(int64_t m, int64_t n, int k, cnmf_dtype a_type);
 cnmf_status launch_prod(const ProdArgs& a, void* ws, size_t ws_bytes,
                         cudaStream_t s);
+// tensor-core path for BF16-stored A (tc.cu)
+bool tc_applicable(const ProdArgs& a);
+size_t tc_workspace(int64_t m, int64_t n, int k);
+cnmf_status launch_prod_tc(const ProdArgs& a, void* ws, int32_t* status,
+                           cudaStream_t s);
+// fix-up of split 128-row output tiles (sketch.cu), FP32 partials
+cnmf_status launch_prod_fixup_f32(void* Z, int64_t ldz, int kz, int64_t P,
+                                  const float* part, int64_t U,
+                                  int64_t chunks, int64_t G, int KP,
+                                  cudaStream_t s);
 
 // ---- CholeskyQR2 on up to two tall panels at once --------------------------
 struct OrthPanel {

@@ -198,7 +198,7 @@ extern "C" cnmf_status cnmf_factor_plain(const void* A, cnmf_dtype a_type,
   char* rinvX = rinvY + (size_t)128 * 128 * e;
   for (int it = 0; it < p->iters; ++it) {
     // X-step: Z = A Y^T; (Y Y^T + lam I)^-1 via Cholesky
-    ProdArgs pa{A, a_type, m, n, lda, false, Yt, r, r, lay.Z, r, r};
+    ProdArgs pa{A, a_type, m, n, lda, false, Yt, r, r, lay.Z, r, r, dev_status};
     CNMF_TRY(launch_prod(pa, lay.prod_ws, lay.prod_bytes, s));
     CNMF_TRY(launch_gram_chol(Yt, r, n, r, w, p->lambda, rinvY, lay.gram_ws,
                               lay.gram_bytes, dev_status, s));
@@ -210,7 +210,7 @@ extern "C" cnmf_status cnmf_factor_plain(const void* A, cnmf_dtype a_type,
     // Y-step with the new X: W = A^T X; (X^T X + phi I)^-1
     CNMF_TRY(launch_gram_chol(X, r, m, r, w, p->phi, rinvX, lay.gram_ws,
                               lay.gram_bytes, dev_status, s));
-    ProdArgs pt{A, a_type, m, n, lda, true, X, r, r, lay.Wn, r, r};
+    ProdArgs pt{A, a_type, m, n, lda, true, X, r, r, lay.Wn, r, r, dev_status};
     CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
     CNMF_TRY(w == CNMF_F64
                  ? rows_dispatch<double>(n, r, lay.Wn, Vt, Phit, Yt, rinvX,

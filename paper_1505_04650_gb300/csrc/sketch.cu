@@ -15,6 +15,7 @@
 // per-CTA partials and summed in CTA order by a fix-up kernel, so results
 // are deterministic and no floating-point atomics are used.
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -314,16 +315,50 @@ static int prod_kp(int k) {
 }
 
 size_t prod_workspace(int64_t m, int64_t n, int k, cnmf_dtype a_type) {
-  (void)m; (void)n;
   // two partial tiles per CTA; at most 4 resident CTAs per SM.
   size_t w = a_type == CNMF_F64 ? 8 : 4;
-  return (size_t)4 * num_sms() * 2 * SK_BP * prod_kp(k) * w + 256;
+  size_t b = (size_t)4 * num_sms() * 2 * SK_BP * prod_kp(k) * w + 256;
+  if (a_type == CNMF_BF16) b = std::max(b, tc_workspace(m, n, k));
+  return b;
+}
+
+cnmf_status launch_prod_fixup_f32(void* Z, int64_t ldz, int kz, int64_t P,
+                                  const float* part, int64_t U,
+                                  int64_t chunks, int64_t G, int KP,
+                                  cudaStream_t s) {
+  const unsigned tiles = (unsigned)ceil_div(P, SK_BP);
+#define FIX_CASE(K)                                                      \
+  case K:                                                                \
+    k_prod_fixup<float, K><<<tiles, 256, 0, s>>>((float*)Z, ldz, kz, P,   \
+                                                 part, U, chunks, G);    \
+    break;
+  switch (KP) {
+    FIX_CASE(16)
+    FIX_CASE(32)
+    FIX_CASE(48)
+    FIX_CASE(64)
+    FIX_CASE(80)
+    FIX_CASE(96)
+    FIX_CASE(128)
+    default: return CNMF_E_INVALID_ARG;
+  }
+#undef FIX_CASE
+  CNMF_CHECK_LAUNCH();
+  return CNMF_OK;
+}
+
+static bool tc_disabled() {
+  static int v = -1;
+  if (v < 0) v = getenv("CNMF_NO_TENSOR_CORES") != nullptr ? 1 : 0;
+  return v == 1;
 }
 
 cnmf_status launch_prod(const ProdArgs& a, void* ws, size_t ws_bytes,
                         cudaStream_t s) {
   if (ws_bytes < prod_workspace(a.m, a.n, std::max(a.kb, a.kz), a.a_type))
     return CNMF_E_WORKSPACE;
+  if (a.a_type == CNMF_BF16 && !tc_disabled() && tc_applicable(a))
+    return launch_prod_tc(a, ws, a.status, s);
   if (a.a_type == CNMF_F64)
     return a.trans ? dispatch_kp<double, double, true>(a, ws, s)
                    : dispatch_kp<double, double, false>(a, ws, s);

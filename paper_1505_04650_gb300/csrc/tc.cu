@@ -1,0 +1,511 @@
+// Tensor-core products with a BF16-stored A (the mixed-precision sketch of
+// the compression, Alg. 1 power scheme on A and A^T):
+//
+//   Z = A B    (output rows i of A; A tile K-major)           trans = false
+//   Z = A^T B  (output rows j = columns of A; A tile MN-major) trans = true
+//
+// B (FP32, S x k) is first packed into bf16 "hi | lo" planes, transposed so
+// that the reduction index is contiguous: Bp[c][s] = bf16(B[s][c]) and
+// Bp[KP + c][s] = bf16(B[s][c] - hi) (|B - hi - lo| <= 2^-18 |B|).  One MMA
+// with N = 2 KP then yields A B_hi and A B_lo side by side in TMEM; the
+// epilogue adds the two halves in FP32.  A is read exactly as stored.
+//
+// Kernel (one CTA per SM, persistent, stream-K split of (output tile,
+// 64-wide reduction chunk) units like the CUDA-core kernel, sharing its
+// fix-up): warp 0 lane 0 issues TMA loads (128-byte swizzle) into an
+// N-stage mbarrier ring; warp 1 allocates TMEM and lane 0 issues
+// tcgen05.mma (M = 128, N = 2 KP, K = 16, FP32 accumulate) into one of two
+// TMEM accumulators; warps 4-7 drain finished accumulators with
+// tcgen05.ld and write FP32 rows (or split-tile partials).  Every wait is
+// bounded: on expiry the kernel records CNMF_E_TIMEOUT, drains its own
+// copies and MMAs (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cnmf {
+
+constexpr int TC_BM = 128;   // output rows per tile (MMA M)
+constexpr int TC_BK = 64;    // reduction elements per stage (128 B of bf16)
+constexpr int TC_NT = 256;   // warp 0 TMA, warp 1 MMA, warps 4-7 epilogue
+
+template <int KP>
+struct TcCfg {
+  static constexpr int N = 2 * KP;
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;   // 16 KiB
+  static constexpr int B_BYTES = N * TC_BK * 2;        // N rows x 128 B
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int ST_FIT = (200 * 1024) / STAGE;
+  static constexpr int STAGES = ST_FIT > 8 ? 8 : ST_FIT;
+  static constexpr int TMEM_COLS = 2 * N <= 64 ? 64
+                                   : 2 * N <= 128 ? 128
+                                   : 2 * N <= 256 ? 256 : 512;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of `parity`; false after ~timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity,
+                                          volatile int* abort_flag,
+                                          int32_t* status) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  uint32_t spins = 0;
+  while (!mbar_try(b, parity)) {
+    if ((++spins & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer_ns() - t0 > 2000000000ull) {
+        set_status(status, CNMF_E_TIMEOUT);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map,
+                                            int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::"
+      "complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+      "[%0];" ::"r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t dtm, uint64_t ad, uint64_t bd,
+                                       uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtm),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, "
+      "%7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+        "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: 128-byte swizzle, version 1 (tcgen05).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo,
+                                          uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, B K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__host__ __device__ __forceinline__ int64_t tc_split_start(int64_t c, int64_t U,
+                                                           int64_t G) {
+  return (c * U) / G;
+}
+
+// ---------------------------------------------------------------------------
+// B (S x kb, FP32, pitch ldb) -> Bp (2 KP x spad, bf16), transposed hi | lo.
+// ---------------------------------------------------------------------------
+__global__ void k_pack_panel(const float* __restrict__ B, int64_t S,
+                             int64_t ldb, int kb, int KP,
+                             bf16* __restrict__ Bp, int64_t spad) {
+  __shared__ float tile[32][33];
+  const int64_t s0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t s = s0 + r;
+    const int c = c0 + tx;
+    tile[r][tx] = (s < S && c < kb) ? B[s * ldb + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc;
+    const int64_t s = s0 + tx;
+    if (c >= KP || s >= spad) continue;
+    const float v = tile[tx][cc];
+    const bf16 hi = __float2bfloat16_rn(v);
+    const bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    Bp[(int64_t)c * spad + s] = hi;
+    Bp[(int64_t)(KP + c) * spad + s] = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The product kernel
+// ---------------------------------------------------------------------------
+template <int KP, bool TRANS>
+__global__ void __launch_bounds__(TC_NT, 1)
+    k_tc_prod(const __grid_constant__ CUtensorMap tmA,
+              const __grid_constant__ CUtensorMap tmB, int64_t P,
+              float* __restrict__ Z, int64_t ldz, int kz,
+              float* __restrict__ part, int64_t U, int64_t chunks,
+              int32_t* status) {
+  typedef TcCfg<KP> C;
+  constexpr int N = C::N;
+  constexpr int ST = C::STAGES;
+  constexpr uint32_t IDESC = idesc_bf16(TC_BM, N, TRANS);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[8], empty_bar[8];
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t G = gridDim.x, c = blockIdx.x;
+  const int64_t u0 = tc_split_start(c, U, G), u1 = tc_split_start(c + 1, U, G);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ST; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf_bar[i], 1);
+      mbar_init(&acce_bar[i], 128);
+    }
+    mbar_init(&drain_bar, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::
+            "r"(smem_u32(&tmem_base_s)),
+        "r"(C::TMEM_COLS)
+        : "memory");
+    asm volatile(
+        "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::
+            : "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t issued_phase[8];
+    bool issued[8];
+    for (int i = 0; i < 8; ++i) { issued[i] = false; issued_phase[i] = 0; }
+    int64_t u = u0;
+    bool ok = true;
+    while (ok && u < u1) {
+      const int64_t tp = u / chunks, ts0 = u % chunks;
+      const int64_t ts1 = min(chunks, ts0 + (u1 - u));
+      for (int64_t ts = ts0; ts < ts1; ++ts) {
+        if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_s, status)) {
+          ok = false;
+          break;
+        }
+        unsigned char* sa = smem + (size_t)stage * C::STAGE;
+        unsigned char* sb = sa + C::A_BYTES;
+        mbar_expect_tx(&full_bar[stage], (uint32_t)C::STAGE);
+        if (!TRANS) {
+          tma_load_2d(sa, &tmA, (int)(ts * TC_BK), (int)(tp * TC_BM),
+                      &full_bar[stage]);
+        } else {
+          tma_load_2d(sa, &tmA, (int)(tp * TC_BM), (int)(ts * TC_BK),
+                      &full_bar[stage]);
+          tma_load_2d(sa + C::A_BYTES / 2, &tmA, (int)(tp * TC_BM + 64),
+                      (int)(ts * TC_BK), &full_bar[stage]);
+        }
+        tma_load_2d(sb, &tmB, (int)(ts * TC_BK), 0, &full_bar[stage]);
+        issued[stage] = true;
+        issued_phase[stage] = phase;
+        if (++stage == ST) { stage = 0; phase ^= 1u; }
+      }
+      u = tp * chunks + ts1;
+    }
+    // drain: every copy this thread issued has landed before teardown
+    for (int i = 0; i < ST; ++i)
+      if (issued[i]) {
+        if (!mbar_try(&full_bar[i], issued_phase[i])) {
+          const uint64_t t0 = globaltimer_ns();
+          while (!mbar_try(&full_bar[i], issued_phase[i]) &&
+                 globaltimer_ns() - t0 < 2000000000ull) {
+          }
+        }
+      }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int ab = 0;
+    uint32_t aphase = 0;
+    bool any = false;
+    int64_t u = u0;
+    bool ok = true;
+    while (ok && u < u1) {
+      const int64_t tp = u / chunks, ts0 = u % chunks;
+      const int64_t ts1 = min(chunks, ts0 + (u1 - u));
+      if (!mbar_wait(&acce_bar[ab], aphase ^ 1u, &abort_s, status)) break;
+      tc_fence_after();
+      const uint32_t dtm = tmem + (uint32_t)(ab * N);
+      for (int64_t ts = ts0; ts < ts1; ++ts) {
+        if (!mbar_wait(&full_bar[stage], phase, &abort_s, status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + (size_t)stage * C::STAGE);
+        const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          uint64_t ad, bd;
+          if (!TRANS) ad = sdesc(sa + kk * 32, 16, 1024);          // K-major
+          else ad = sdesc(sa + kk * 2048, C::A_BYTES / 2, 1024);   // MN-major
+          bd = sdesc(sb + kk * 32, 16, 1024);
+          tc_mma(dtm, ad, bd, IDESC, (ts > ts0 || kk > 0) ? 1u : 0u);
+          any = true;
+        }
+        tc_commit(&empty_bar[stage]);
+        if (++stage == ST) { stage = 0; phase ^= 1u; }
+      }
+      if (!ok) break;
+      tc_commit(&accf_bar[ab]);
+      if (++ab == 2) { ab = 0; aphase ^= 1u; }
+      u = tp * chunks + ts1;
+    }
+    if (any) {   // all MMAs complete before TMEM is released
+      tc_commit(&drain_bar);
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try(&drain_bar, 0) && globaltimer_ns() - t0 < 2000000000ull) {
+      }
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue ----------------
+    const int q = warp - 4;                 // TMEM lane quarter
+    const int row = 32 * q + lane;
+    int ab = 0;
+    uint32_t aphase = 0;
+    int64_t u = u0;
+    bool first = true;
+    while (u < u1) {
+      const int64_t tp = u / chunks, ts0 = u % chunks;
+      const int64_t ts1 = min(chunks, ts0 + (u1 - u));
+      if (!mbar_wait(&accf_bar[ab], aphase, &abort_s, status)) break;
+      tc_fence_after();
+      const bool whole = (ts0 == 0 && ts1 == chunks);
+      const int64_t p = tp * TC_BM + row;
+      float* dst = whole ? (p < P ? Z + p * ldz : nullptr)
+                         : part + (((size_t)c * 2 + (first ? 0 : 1)) * TC_BM +
+                                   row) * KP;
+      const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * N);
+#pragma unroll 1
+      for (int c0 = 0; c0 < KP; c0 += 16) {
+        float hi[16], lo[16];
+        tc_ld16(tbase + c0, hi);
+        tc_ld16(tbase + KP + c0, lo);
+        if (dst) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int col = c0 + t;
+            if (!whole || col < kz) dst[col] = hi[t] + lo[t];
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acce_bar[ab]);
+      if (++ab == 2) { ab = 0; aphase ^= 1u; }
+      first = false;
+      u = tp * chunks + ts1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
+                     tmem),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+static bool make_map(CUtensorMap* m, const void* base, uint64_t inner,
+                     uint64_t outer, uint64_t row_bytes, uint32_t box_inner,
+                     uint32_t box_outer) {
+  auto enc = tmap_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int tc_kp(int k) { return pad_k(k); }
+
+size_t tc_workspace(int64_t m, int64_t n, int k) {
+  const int KP = tc_kp(k);
+  const int64_t spad = (std::max(m, n) + 7) / 8 * 8;
+  size_t b = 0;
+  b += (((size_t)num_sms() * 2 * TC_BM * KP * 4) + 255) & ~size_t(255);
+  b += (((size_t)2 * KP * spad * 2) + 255) & ~size_t(255);
+  return b + 256;
+}
+
+bool tc_applicable(const ProdArgs& a) {
+  if (a.a_type != CNMF_BF16) return false;
+  if ((uintptr_t)a.A % 16 != 0 || (a.lda * 2) % 16 != 0) return false;
+  if (std::max(a.kb, a.kz) > 128 || a.m < 1 || a.n < 1) return false;
+  if (a.m >= (1ll << 31) || a.n >= (1ll << 31)) return false;
+  return tmap_encoder() != nullptr;
+}
+
+template <int KP, bool TRANS>
+static cnmf_status run_tc(const ProdArgs& a, void* ws, int32_t* status,
+                          cudaStream_t s) {
+  typedef TcCfg<KP> C;
+  static std::once_flag once;
+  static bool smem_ok = false;
+  std::call_once(once, [] {
+    smem_ok = set_max_smem((const void*)k_tc_prod<KP, TRANS>, C::SMEM);
+  });
+  if (!smem_ok) return CNMF_E_INVALID_ARG;
+  const int64_t P = TRANS ? a.n : a.m;
+  const int64_t S = TRANS ? a.m : a.n;
+  const int64_t spad = (S + 7) / 8 * 8;
+  Carve cv(ws, SIZE_MAX);
+  float* part = cv.take<float>((size_t)num_sms() * 2 * TC_BM * KP);
+  bf16* Bp = cv.take<bf16>((size_t)2 * KP * spad);
+  // pack B
+  dim3 pg((unsigned)ceil_div(spad, 32), (unsigned)ceil_div(KP, 32));
+  k_pack_panel<<<pg, 256, 0, s>>>((const float*)a.B, S, a.ldb, a.kb, KP, Bp,
+                                  spad);
+  CNMF_CHECK_LAUNCH();
+  CUtensorMap ta, tb;
+  bool ok;
+  if (!TRANS)
+    ok = make_map(&ta, a.A, (uint64_t)a.n, (uint64_t)a.m, (uint64_t)a.lda * 2,
+                  TC_BK, TC_BM);
+  else
+    ok = make_map(&ta, a.A, (uint64_t)a.n, (uint64_t)a.m, (uint64_t)a.lda * 2,
+                  64, TC_BK);
+  ok = ok && make_map(&tb, Bp, (uint64_t)spad, (uint64_t)(2 * KP),
+                      (uint64_t)spad * 2, TC_BK, 2 * KP);
+  if (!ok) return CNMF_E_INVALID_ARG;
+  const int64_t tiles = ceil_div(P, TC_BM);
+  const int64_t chunks = std::max<int64_t>(1, ceil_div(S, TC_BK));
+  const int64_t U = tiles * chunks;
+  const int64_t G = std::min<int64_t>(U, num_sms());
+  k_tc_prod<KP, TRANS><<<(unsigned)G, TC_NT, C::SMEM, s>>>(
+      ta, tb, P, (float*)a.Z, a.ldz, a.kz, part, U, chunks, status);
+  CNMF_CHECK_LAUNCH();
+  if (chunks > 1)
+    CNMF_TRY(launch_prod_fixup_f32(a.Z, a.ldz, a.kz, P, part, U, chunks, G, KP,
+                                   s));
+  return CNMF_OK;
+}
+
+cnmf_status launch_prod_tc(const ProdArgs& a, void* ws, int32_t* status,
+                           cudaStream_t s) {
+  const int KP = tc_kp(std::max(a.kb, a.kz));
+#define TC_CASE(K)                                                  \
+  case K:                                                           \
+    return a.trans ? run_tc<K, true>(a, ws, status, s)              \
+                   : run_tc<K, false>(a, ws, status, s);
+  switch (KP) {
+    TC_CASE(16)
+    TC_CASE(32)
+    TC_CASE(48)
+    TC_CASE(64)
+    TC_CASE(80)
+    TC_CASE(96)
+    TC_CASE(128)
+  }
+#undef TC_CASE
+  return CNMF_E_INVALID_ARG;
+}
+
+}  // namespace cnmf

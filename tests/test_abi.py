@@ -80,7 +80,7 @@ def test_invalid_arguments_rejected_on_host(lib):
                              fake, 1 << 20, nul) == E   # f64 A with f32 U
     assert lib.cnmf_gaussian(0, 0, -1, 3, 1, fake, nul) == E
     assert lib.cnmf_sketch_pass(fake, 1, 10, 10, 10, 0, fake, nul, fake, nul,
-                                fake, 1 << 20, nul) == E
+                                fake, 1 << 20, nul, nul) == E
 
 
 def test_workspace_queries(lib):

@@ -67,11 +67,18 @@ def test_sketch_pass_products(storage, m, n, k):
     Ad = to_dev(As, storage)
     Xd = torch.tensor(X, dtype=wdt(storage)).cuda()
     Yd = torch.tensor(Y, dtype=wdt(storage)).cuda()
-    Zm, Zn = cn.cnmf_sketch_pass(Ad, Xd, Yd)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Zm, Zn = cn.cnmf_sketch_pass(Ad, Xd, Yd, status=st)
     torch.cuda.synchronize()
+    assert int(st.item()) == 0
     u = unit(storage)
-    ref_m, bnd_m = Aw @ X, (n + 2) * u * (np.abs(Aw) @ np.abs(X))
-    ref_n, bnd_n = Aw.T @ Y, (m + 2) * u * (np.abs(Aw).T @ np.abs(Y))
+    # BF16 A runs on the tensor cores: FP32 accumulation (allow 2u per add)
+    # plus the 2^-18 residual of the bf16 hi + lo split of X / Y
+    acc, split = (2 * u, 2.0 ** -17) if storage == "bf16" else (u, 0.0)
+    ref_m = Aw @ X
+    bnd_m = ((n + 2) * acc + split) * (np.abs(Aw) @ np.abs(X))
+    ref_n = Aw.T @ Y
+    bnd_n = ((m + 2) * acc + split) * (np.abs(Aw).T @ np.abs(Y))
     assert np.all(np.abs(to_np(Zm) - ref_m) <= bnd_m + 1e-300)
     assert np.all(np.abs(to_np(Zn) - ref_n) <= bnd_n + 1e-300)
 
