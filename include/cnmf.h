@@ -203,6 +203,49 @@ cnmf_status cnmf_factor(const void* L, const void* Rt, const void* Atilde,
                         cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_factor_batched: `sweeps` compressed ADMM sweeps (Alg. 4, FP32) for
+ * each of `nitems` independent problems in ONE launch.  Each problem runs
+ * on a cluster of `cluster_size` CTAs (1, 2, 4 or 8) that split its rows
+ * and add their shares through distributed shared memory; there are no
+ * grid-wide waits, and a problem's result does not depend on the other
+ * problems in the launch.  A problem may run its sweeps over several
+ * launches; the result is bitwise that of one launch with the total count.
+ *   items   DEVICE array of nitems cnmf_batch_item (below); a slot with
+ *           L == NULL or r == 0 is skipped.  Each item's buffers are its
+ *           own: L (m x d), Rt (n x d), Atilde (d x d) from cnmf_compress;
+ *           U (m x r) and Vt (n x r) in/out; state as in cnmf_factor
+ *           (cnmf_factor_state_bytes, FP32); scratch of
+ *           cnmf_batch_scratch_bytes(r, d) bytes kept between launches.
+ *           flags & CNMF_BATCH_FRESH: start from U, V as given (Alg. 4
+ *           setup: Yt = V R^T, Lam = Phi = 0); clear it for later launches.
+ *   max_r, max_d  bounds on the items' r and d (r <= 32, d <= 64, r <= d);
+ *           they select the kernel variant and its shared-memory size.
+ * The launch reads `items` when it runs, so a CUDA graph that captured it
+ * can be replayed after the caller rewrites the device array.
+ * ---------------------------------------------------------------------- */
+#define CNMF_BATCH_FRESH 1
+typedef struct {
+  const void* L;
+  const void* Rt;
+  const void* Atilde;
+  void* U;
+  void* Vt;
+  void* state;
+  void* scratch;
+  int64_t m, n;
+  int32_t r, d;
+  double lambda, phi, xi;
+  int32_t flags;
+  int32_t reserved;
+} cnmf_batch_item;
+
+size_t cnmf_batch_scratch_bytes(int32_t r, int32_t d);
+cnmf_status cnmf_factor_batched(const cnmf_batch_item* items, int32_t nitems,
+                                int32_t sweeps, int32_t cluster_size,
+                                int32_t max_r, int32_t max_d,
+                                int32_t* dev_status, cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_factor_plain: the uncompressed ADMM NMF baseline -- Alg. 4 with
  * L = I_m, R = I_n, Atilde = A (Sec. III, problem nmfEquiv; Xu et al.).
  * Each sweep reads A twice (A Y^T, then A^T X with the new X).

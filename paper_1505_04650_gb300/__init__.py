@@ -25,7 +25,7 @@ __all__ = [
     "CnmfError", "lib", "cnmf_gaussian", "cnmf_philox_words",
     "cnmf_sketch_pass", "cnmf_orth", "cnmf_compress", "cnmf_factor",
     "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
-    "sketch_size", "default_penalty",
+    "sketch_size", "default_penalty", "BatchProblem", "cnmf_factor_batched",
 ]
 
 
@@ -330,3 +330,78 @@ def cnmf_residual(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,
                             _ptr(Vt), _DT[w], r, _ptr(out), _ptr(ws),
                             ws.numel(), _stream(dev)), "cnmf_residual")
     return out
+
+
+# --------------------------------------------------------------------------
+class BatchProblem:
+    """Device buffers of one problem for cnmf_factor_batched (FP32).
+
+    Holds L, Rt, Atilde (from cnmf_compress), U, Vt (in/out), the resumable
+    state and the scratch the batched kernel keeps between launches."""
+
+    def __init__(self, L, Rt, Atilde, U, Vt, lam, phi, xi=1.0):
+        m, d = L.shape
+        n = Rt.shape[0]
+        r = U.shape[1]
+        for t, shp, nm in ((L, (m, d), "L"), (Rt, (n, d), "Rt"),
+                           (Atilde, (d, d), "Atilde"), (U, (m, r), "U"),
+                           (Vt, (n, r), "Vt")):
+            _dense(t, shp, torch.float32, nm)
+        lb = lib()
+        self.L, self.Rt, self.Atilde, self.U, self.Vt = L, Rt, Atilde, U, Vt
+        self.m, self.n, self.r, self.d = m, n, r, d
+        self.lam, self.phi, self.xi = float(lam), float(phi), float(xi)
+        nbs = lb.cnmf_factor_state_bytes(m, n, r, d, _lib.CNMF_F32)
+        self.state = FactorState(torch.zeros(nbs, dtype=torch.uint8,
+                                             device=L.device), m, n, r, d,
+                                 torch.float32)
+        self.scratch = torch.zeros(lb.cnmf_batch_scratch_bytes(r, d),
+                                   dtype=torch.uint8, device=L.device)
+        self.fresh = True
+
+    def item(self) -> "_lib.BatchItem":
+        p = lambda t: t.data_ptr()
+        return _lib.BatchItem(p(self.L), p(self.Rt), p(self.Atilde), p(self.U),
+                              p(self.Vt), p(self.state.buf), p(self.scratch),
+                              self.m, self.n, self.r, self.d, self.lam,
+                              self.phi, self.xi,
+                              _lib.CNMF_BATCH_FRESH if self.fresh else 0, 0)
+
+
+def pack_items(problems) -> bytes:
+    """Host image of a cnmf_batch_item array (None -> empty slot)."""
+    arr = (_lib.BatchItem * max(1, len(problems)))()
+    for i, pb in enumerate(problems):
+        if pb is not None:
+            arr[i] = pb.item()
+    return bytes(arr)
+
+
+def cnmf_factor_batched(problems, sweeps: int, cluster_size: int = 1,
+                        items_dev: torch.Tensor | None = None,
+                        status: torch.Tensor | None = None,
+                        max_r: int | None = None, max_d: int | None = None):
+    """`sweeps` compressed ADMM sweeps for every problem in one launch.
+
+    `problems` is a list of BatchProblem (or None for an empty slot).  The
+    item array is copied to `items_dev` (a device uint8 tensor, allocated if
+    None) before the launch; after it every problem's fresh flag is
+    cleared.  Returns (items_dev, status)."""
+    live = [p for p in problems if p is not None]
+    if not live:
+        return items_dev, status
+    dev = live[0].L.device
+    img = pack_items(problems)
+    if items_dev is None or items_dev.numel() < len(img):
+        items_dev = torch.empty(len(img), dtype=torch.uint8, device=dev)
+    host = torch.frombuffer(bytearray(img), dtype=torch.uint8)
+    items_dev[:len(img)].copy_(host, non_blocking=False)
+    st = status if status is not None else _status(dev)
+    mr = max_r or max(p.r for p in live)
+    md = max_d or max(p.d for p in live)
+    _check(lib().cnmf_factor_batched(_ptr(items_dev), len(problems), sweeps,
+                                     cluster_size, mr, md, _ptr(st),
+                                     _stream(dev)), "cnmf_factor_batched")
+    for p in live:
+        p.fresh = False
+    return items_dev, st

@@ -27,6 +27,19 @@ class AdmmParams(C.Structure):
                 ("reserved", c_int32)]
 
 
+CNMF_BATCH_FRESH = 1
+
+
+class BatchItem(C.Structure):
+    """cnmf_batch_item (include/cnmf.h)."""
+    _fields_ = [("L", c_void_p), ("Rt", c_void_p), ("Atilde", c_void_p),
+                ("U", c_void_p), ("Vt", c_void_p), ("state", c_void_p),
+                ("scratch", c_void_p), ("m", c_int64), ("n", c_int64),
+                ("r", c_int32), ("d", c_int32), ("lambda_", c_double),
+                ("phi", c_double), ("xi", c_double), ("flags", c_int32),
+                ("reserved", c_int32)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "cnmf_status_string": (C.c_char_p, [c_int32]),
@@ -78,6 +91,9 @@ SIGNATURES = {
     "cnmf_residual_noalloc": (c_int32, [c_void_p, c_int32, c_int64, c_int64,
                                         c_int64, c_void_p, c_void_p, c_int32,
                                         c_int32, c_void_p, c_void_p]),
+    "cnmf_batch_scratch_bytes": (c_size_t, [c_int32, c_int32]),
+    "cnmf_factor_batched": (c_int32, [c_void_p, c_int32, c_int32, c_int32,
+                                      c_int32, c_int32, c_void_p, c_void_p]),
     "cnmf_barrier_selftest": (c_int32, [c_int32, c_int32, c_int32, c_int32,
                                         c_void_p, c_size_t, c_void_p,
                                         c_void_p, c_void_p]),

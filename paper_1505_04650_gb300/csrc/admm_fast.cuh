@@ -59,7 +59,7 @@ __device__ __forceinline__ void quad_mm(W* C, int RP, const W* A, int sap,
                                         int sas, const W* B, int P, int S,
                                         W scale, const W* init_g, int init_ld,
                                         int init_cols, W diag, int task0,
-                                        int ntask_total) {
+                                        bool init_smem) {
   const int Q = RP / 4;
   for (int t = threadIdx.x - task0; t < P * Q; t += AD_NT) {
     if (t < 0) continue;
@@ -69,8 +69,10 @@ __device__ __forceinline__ void quad_mm(W* C, int RP, const W* A, int sap,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int col = 4 * q + j;
-      ini[j] = (init_g && col < init_cols) ? __ldcg(init_g + p * init_ld + col)
-                                           : W(0);
+      ini[j] = W(0);
+      if (init_g && col < init_cols)
+        ini[j] = init_smem ? init_g[p * init_ld + col]
+                           : __ldcg(init_g + p * init_ld + col);
     }
     const W* ap = A + p * sap;
     const W* bp = B + 4 * q;
@@ -94,7 +96,6 @@ __device__ __forceinline__ void quad_mm(W* C, int RP, const W* A, int sap,
       C[p * RP + col] = o[j];
     }
   }
-  (void)ntask_total;
 }
 
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
@@ -159,9 +160,13 @@ __device__ void fast_sweep_inverse(W* G, W* vbuf, int r, int RP,
   __syncthreads();
 }
 
+// SX, SY^T: the reduced shares (global memory written by other CTAs, read
+// through L2, or this CTA's shared memory when sxy_smem).
 template <typename W, int RMAX>
 __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
-                           uint64_t* sub = nullptr) {
+                           uint64_t* sub = nullptr, const W* SXp = nullptr,
+                           const W* SYp = nullptr, bool sxy_smem = false) {
+  if (!SXp) { SXp = a.SX; SYp = a.SY; }
   const int r = a.r, d = a.d, RP = o.RP, Q = RP / 4;
   uint64_t tm = sub ? globaltimer_ns() : 0;
   auto mark = [&](int i) {
@@ -173,27 +178,27 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
   W* M = sm + o.M;
   W* G = sm + o.G;
   // M = SX + At Yt^T  (d x RP);  G = Yt Yt^T + lam I  (r x RP)
-  quad_mm<W>(M, RP, At, d, 1, YtT, d, d, W(1), a.SX, r, r, W(0), 0, 0);
+  quad_mm<W>(M, RP, At, d, 1, YtT, d, d, W(1), SXp, r, r, W(0), 0, sxy_smem);
   quad_mm<W>(G, RP, YtT, 1, RP, YtT, r, d, W(1), nullptr, 0, r, a.lam,
-             d * Q, 0);
+             d * Q, false);
   __syncthreads();
   mark(0);
   fast_sweep_inverse<W, RMAX>(G, sm + o.v, r, RP, a.status);
   mark(1);
   // Xt = M (Yt Yt^T + lam I)^-1 = -M G
-  quad_mm<W>(Xt, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, 0);
+  quad_mm<W>(Xt, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
   __syncthreads();
   mark(2);
   // M = SY^T + At^T Xt (d x RP);  G = Xt^T Xt + phi I
-  quad_mm<W>(M, RP, At, 1, d, Xt, d, d, W(1), a.SY, r, r, W(0), 0, 0);
+  quad_mm<W>(M, RP, At, 1, d, Xt, d, d, W(1), SYp, r, r, W(0), 0, sxy_smem);
   quad_mm<W>(G, RP, Xt, 1, RP, Xt, r, d, W(1), nullptr, 0, r, a.phi,
-             d * Q, 0);
+             d * Q, false);
   __syncthreads();
   mark(3);
   fast_sweep_inverse<W, RMAX>(G, sm + o.v, r, RP, a.status);
   mark(4);
   // Yt^T = M (Xt^T Xt + phi I)^-1 = -M G
-  quad_mm<W>(YtT, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, 0);
+  quad_mm<W>(YtT, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
   __syncthreads();
   mark(5);
   for (int e = threadIdx.x; e < d * r; e += AD_NT) {
@@ -208,20 +213,21 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
 // added over lanes in lane order.  mode 0: fresh setup (Lam = Phi = 0,
 // shares of lam U and phi V, plus Yt0^T = R V^T); mode 1: resume setup;
 // mode 2: ADMM row updates.
+// This CTA is part c of G splitting the rows; its shares go to dst
+// (3 d r entries: SX, SY^T, Yt0^T).
 template <typename W, int DMAX, bool RES>
 __device__ void sweep_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
-                           int mode, uint64_t* sub = nullptr) {
+                           int mode, uint64_t* sub, int64_t G, int64_t c,
+                           W* dst) {
   uint64_t tm = sub ? globaltimer_ns() : 0;
   auto mark = [&](int i) {
     if (sub) { uint64_t t = globaltimer_ns(); sub[i] += t - tm; tm = t; }
   };
   const int r = a.r, d = a.d, dp = o.dp, RP = o.RP, nl = o.nl;
-  const int64_t G = gridDim.x, c = blockIdx.x;
   const int b = threadIdx.x % r, lr = threadIdx.x / r;
   const bool active = lr < nl;
   const int dr = d * r;
   W* Red = sm + o.Red;
-  W* dst = a.part + (size_t)c * (3 * dr);
   for (int side = 0; side < 2 + (mode == 0 ? 1 : 0); ++side) {
     const bool vside = side > 0;
     const int64_t tot = vside ? a.n : a.m;
@@ -382,7 +388,8 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   if (RES) fast_resident_copy<W>(a, sm, o, 0);
   __syncthreads();
 
-  sweep_fast<W, DMAX, RES>(a, sm, o, a.resume ? 1 : 0);
+  sweep_fast<W, DMAX, RES>(a, sm, o, a.resume ? 1 : 0, nullptr, gridDim.x,
+                           blockIdx.x, a.part + (size_t)blockIdx.x * 3 * d * r);
   if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
   reduce_fast<W>(a, a.resume ? 0 : 1);
   if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
@@ -395,7 +402,9 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
     uint64_t t0 = prof ? globaltimer_ns() : 0;
     small_fast<W, RMAX>(a, sm, o, prof ? tsub : nullptr);
     uint64_t t1 = prof ? globaltimer_ns() : 0;
-    sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 7 : nullptr);
+    sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 7 : nullptr,
+                             gridDim.x, blockIdx.x,
+                             a.part + (size_t)blockIdx.x * 3 * d * r);
     uint64_t t2 = prof ? globaltimer_ns() : 0;
     if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
     uint64_t t3 = prof ? globaltimer_ns() : 0;

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #pragma once
+#include <cooperative_groups.h>
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -372,6 +373,7 @@ __global__ void __launch_bounds__(AD_NT) k_admm(AdmmArgs<W> a) {
 }
 
 #include "admm_fast.cuh"
+#include "admm_batch.cuh"
 
 inline size_t state_bytes(int64_t m, int64_t n, int r, int d, size_t e) {
   size_t b = ((size_t)m * r + (size_t)n * r + 2 * (size_t)r * d) * e;

@@ -1,0 +1,297 @@
+"""Serving loop for compressed-NMF requests with continuous batching.
+
+Requests (each one factorization: its own A of shape m x n, rank r, sketch
+size d, q power iterations, a number of ADMM sweeps) arrive over time.  The
+server
+
+* admits waiting requests in arrival order while the device-memory budget
+  (bytes of A, the compression panels, factors, state and scratch) and the
+  slot count allow;
+* draws each admitted request's synthetic A and compresses it
+  (cnmf_compress) on one of a few side streams, so compression of new
+  requests overlaps the sweeps of running ones;
+* runs the compressed ADMM sweeps of all compressed requests in rounds:
+  one batched launch per cluster size (cnmf_factor_batched, replayed from a
+  captured CUDA graph) advances every running request by `sweeps_per_round`
+  sweeps; requests join at the next round after their compression and leave
+  when their sweep count is reached (iteration-level continuous batching);
+* on completion computes the relative residual (cnmf_residual) and frees
+  the request's memory.
+
+Each request's arithmetic is independent of the others (batched kernel
+property), so its result is the same whether it is served alone or in a
+mix.  Latency = completion time - arrival time (host clock).
+"""
+from __future__ import annotations
+
+import collections
+import ctypes as C
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import (BatchProblem, _lib, cnmf_compress, cnmf_residual, lib,
+               raise_on_status)
+from .autotune import Autotuner
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrive: float
+    m: int
+    n: int
+    r: int
+    d: int
+    q: int = 4
+    iters: int = 200
+    sigma: float = 0.01
+    seed: int = 0
+    # filled by the server
+    t_admit: float = math.nan
+    t_compressed: float = math.nan
+    t_done: float = math.nan
+    cluster_size: int = 1
+    rho: float = math.nan
+    floor: float = math.nan
+    nbytes: int = 0
+    done_sweeps: int = 0
+    problem: BatchProblem | None = None
+    A: torch.Tensor | None = None
+    event: torch.cuda.Event | None = None
+    stream_idx: int = 0
+    keep: bool = False          # keep U, Vt after completion
+    U: torch.Tensor | None = None
+    Vt: torch.Tensor | None = None
+
+
+def make_workload(nreq: int, rate: float, seed: int = 0, m_range=(200, 4000),
+                  r_range=(5, 32), q: int = 4, iters: int = 200,
+                  sigma: float = 0.01) -> list[Request]:
+    """Poisson arrivals at `rate` requests/s (rate <= 0: all at t = 0);
+    m, n ~ U[m_range], r ~ U{r_range}, d = r + 10."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    gaps = g.exponential(1.0 / rate, nreq) if rate > 0 else np.zeros(nreq)
+    t = np.cumsum(gaps) - (gaps[0] if rate > 0 else 0.0)
+    reqs = []
+    for i in range(nreq):
+        m = int(g.integers(m_range[0], m_range[1] + 1))
+        n = int(g.integers(m_range[0], m_range[1] + 1))
+        r = int(g.integers(r_range[0], r_range[1] + 1))
+        reqs.append(Request(i, float(t[i]), m, n, r, r + 10, q, iters, sigma,
+                            seed=10_000 * (seed + 1) + i))
+    return reqs
+
+
+def request_bytes(rq: Request) -> int:
+    e = 4
+    m, n, r, d = rq.m, rq.n, rq.r, rq.d
+    b = m * n * e                                  # A
+    b += (m + n) * d * e + d * d * e               # L, Rt, Atilde
+    b += (m + n) * r * e * 2                       # U, Vt, Lam, Phit
+    b += 2 * r * d * e * 2 + 256 * 4               # state tail, scratch
+    return b
+
+
+class Server:
+    def __init__(self, hbm_budget: float = 40e9, max_slots: int = 512,
+                 sweeps_per_round: int = 10, compress_streams: int = 4,
+                 tuner: Autotuner | None = None, use_graphs: bool = True,
+                 device="cuda"):
+        self.dev = torch.device(device)
+        self.budget = int(hbm_budget)
+        self.max_slots = max_slots
+        self.S = sweeps_per_round
+        self.tuner = tuner or Autotuner()
+        self.use_graphs = use_graphs
+        self.main = torch.cuda.current_stream(self.dev)
+        self.side = [torch.cuda.Stream(self.dev) for _ in range(compress_streams)]
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        self.comp_ws = [None] * compress_streams
+        self.groups: dict[int, dict] = {}
+        self.lib = lib()
+
+    # ---- batched launches (one per cluster size), optionally graphed ----
+    def _group(self, key) -> dict:
+        if key not in self.groups:
+            nbytes = C.sizeof(_lib.BatchItem) * self.max_slots
+            self.groups[key] = {
+                "items": torch.zeros(nbytes, dtype=torch.uint8, device=self.dev),
+                "host": torch.zeros(nbytes, dtype=torch.uint8).pin_memory(),
+                "graph": None,
+            }
+        return self.groups[key]
+
+    def _launch(self, key, g: dict):
+        cs, dm = key
+        rc = self.lib.cnmf_factor_batched(
+            C.c_void_p(g["items"].data_ptr()), self.max_slots, self.S, cs, 32,
+            dm, C.c_void_p(self.status.data_ptr()),
+            C.c_void_p(torch.cuda.current_stream(self.dev).cuda_stream))
+        if rc != 0:
+            raise RuntimeError(f"cnmf_factor_batched: status {rc}: "
+                               f"{self.lib.cnmf_last_error().decode()}")
+
+    def _round(self, key, reqs: list[Request]):
+        g = self._group(key)
+        arr = (_lib.BatchItem * self.max_slots)()
+        for i, rq in enumerate(reqs):
+            arr[i] = rq.problem.item()
+        g["host"].numpy()[:] = np.frombuffer(bytes(arr), dtype=np.uint8)
+        g["items"].copy_(g["host"], non_blocking=True)
+        if not self.use_graphs:
+            self._launch(key, g)
+        else:
+            if g["graph"] is None:
+                # warm the kernel variant outside capture, on empty slots
+                scratch = torch.zeros_like(g["items"])
+                save = g["items"]
+                g["items"] = scratch
+                self._launch(key, g)
+                g["items"] = save
+                torch.cuda.synchronize(self.dev)
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=torch.cuda.Stream(self.dev)):
+                    self._launch(key, g)
+                g["graph"] = graph
+                # the captured launch reads the item array when replayed
+                g["items"].copy_(g["host"], non_blocking=True)
+            g["graph"].replay()
+        for rq in reqs:
+            rq.problem.fresh = False
+            rq.done_sweeps += self.S
+
+    def prepare(self, requests: list[Request]):
+        """Tune every size bucket the requests touch before serving."""
+        for rq in requests:
+            self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
+
+    # ---- request lifecycle ----
+    def _admit(self, rq: Request, k: int, now: float):
+        import synth
+        rq.t_admit = now
+        rq.stream_idx = k % len(self.side)
+        s = self.side[rq.stream_idx]
+        with torch.cuda.stream(s):
+            rq.A = synth.lowrank_torch(rq.m, rq.n, rq.r, rq.sigma, rq.seed,
+                                       device=self.dev)
+            U0, Vt0 = synth.init_torch(rq.m, rq.n, rq.r, rq.seed + 1,
+                                       device=self.dev)
+            nb = self.lib.cnmf_compress_workspace(rq.m, rq.n, rq.d, 1)
+            ws = self.comp_ws[rq.stream_idx]
+            if ws is None or ws.numel() < nb:
+                ws = torch.empty(int(nb * 1.25) + 256, dtype=torch.uint8,
+                                 device=self.dev)
+                self.comp_ws[rq.stream_idx] = ws
+            L, Rt, At, _ = cnmf_compress(rq.A, rq.r, rq.d, rq.q, rq.seed + 2,
+                                         status=self.status, ws=ws)
+            rq.problem = BatchProblem(L, Rt, At, U0, Vt0, 1.0, 1.0)
+            rq.event = torch.cuda.Event()
+            rq.event.record(s)
+        rq.cluster_size = self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
+
+    def _ready(self, rq: Request, now: float):
+        # penalty: lambda = phi = ||Atilde||_F / r (needs Atilde on host)
+        pb = rq.problem
+        At = pb.Atilde
+        lam = float(torch.linalg.norm(At.double())) / rq.r
+        pb.lam = pb.phi = lam
+        s = torch.linalg.svdvals(At.double().cpu())
+        rq.floor_num = float((s[: rq.r] ** 2).sum())
+        for t in (pb.L, pb.Rt, pb.Atilde, pb.U, pb.Vt, pb.state.buf,
+                  pb.scratch, rq.A):
+            t.record_stream(self.main)
+        rq.t_compressed = now
+
+    def _finish(self, rq: Request, res: torch.Tensor):
+        e2, a2 = float(res[0]), float(res[1])
+        rq.rho = math.sqrt(e2 / a2)
+        rq.floor = math.sqrt(max(0.0, 1.0 - rq.floor_num / a2))
+        if rq.keep:
+            rq.U = rq.problem.U.clone()
+            rq.Vt = rq.problem.Vt.clone()
+        rq.problem = None
+        rq.A = None
+
+    def run(self, requests: list[Request], realtime: bool = True) -> dict:
+        pending = collections.deque(sorted(requests, key=lambda q: q.t_arrive))
+        waiting: collections.deque = collections.deque()
+        compressing: list[Request] = []
+        running: list[Request] = []
+        done: list[Request] = []
+        in_use = 0
+        k = 0
+        rounds = 0
+        t0 = time.perf_counter()
+        clock = lambda: time.perf_counter() - t0
+        total = len(requests)
+        while len(done) < total:
+            now = clock()
+            while pending and (pending[0].t_arrive <= now or not realtime):
+                waiting.append(pending.popleft())
+            # admission by memory budget and slots
+            while waiting:
+                rq = waiting[0]
+                need = request_bytes(rq)
+                slots = len(compressing) + len(running)
+                if slots >= self.max_slots or (in_use + need > self.budget
+                                               and slots > 0):
+                    break
+                waiting.popleft()
+                rq.nbytes = need
+                in_use += need
+                self._admit(rq, k, clock())
+                k += 1
+                compressing.append(rq)
+            # compressed requests join the batch at this round
+            still = []
+            for rq in compressing:
+                if rq.event.query():
+                    self._ready(rq, clock())
+                    running.append(rq)
+                else:
+                    still.append(rq)
+            compressing = still
+            if running:
+                groups: dict = collections.defaultdict(list)
+                for rq in running:
+                    groups[(rq.cluster_size, 32 if rq.d <= 32 else 64)].append(rq)
+                for key, reqs in groups.items():
+                    for i in range(0, len(reqs), self.max_slots):
+                        self._round(key, reqs[i:i + self.max_slots])
+                rounds += 1
+                finished = [rq for rq in running if rq.done_sweeps >= rq.iters]
+                running = [rq for rq in running if rq.done_sweeps < rq.iters]
+                outs = []
+                for rq in finished:
+                    outs.append(cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt))
+                torch.cuda.synchronize(self.dev)
+                now = clock()
+                for rq, res in zip(finished, outs):
+                    rq.t_done = now
+                    res_h = res.cpu()
+                    self._finish(rq, res_h)
+                    in_use -= rq.nbytes
+                    done.append(rq)
+            elif compressing:
+                torch.cuda.synchronize(self.dev)
+            elif pending and realtime:
+                time.sleep(max(0.0, min(0.001, pending[0].t_arrive - clock())))
+        raise_on_status(self.status, "serving")
+        wall = clock()
+        lat = np.array([rq.t_done - rq.t_arrive for rq in done]) * 1e3
+        ok = np.array([rq.rho <= rq.floor + 1e-3 for rq in done])
+        return {
+            "requests": total, "wall_s": wall,
+            "factorizations_per_s": total / wall,
+            "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()),
+            "frac_at_target": float(ok.mean()),
+            "rounds": rounds, "sweeps_per_round": self.S,
+            "cluster_sizes": {str(c): int(sum(rq.cluster_size == c for rq in done))
+                              for c in (1, 2, 4, 8)},
+        }

@@ -31,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "CONFIGS", "lowrank", "separable", "init_factors", "gaussian",
-    "as_storage", "bf16_round", "widen",
+    "as_storage", "bf16_round", "widen", "lowrank_torch", "init_torch",
 ]
 
 # Workload shapes: a small FP64 case, the large FP32 case, the wide separable
@@ -161,3 +161,36 @@ def as_storage(A64: np.ndarray, storage: str) -> np.ndarray:
     if storage == "bf16":
         return bf16_round(A64)
     raise ValueError(storage)
+
+
+def lowrank_torch(m: int, n: int, r: int, sigma: float, seed: int,
+                  device="cuda"):
+    """The low-rank recipe drawn with PyTorch's generator on `device`
+    (X0, then Y0, then the noise; FP32), for workloads too large to draw on
+    the host.  The same (shape, seed, device type) gives the same matrix;
+    copy it to the host to feed the oracle."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    X0 = torch.rand(m, r, generator=g, device=device)
+    Y0 = torch.rand(r, n, generator=g, device=device)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        A = X0 @ Y0
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    if sigma > 0:
+        A += torch.randn(m, n, generator=g, device=device).abs_() * sigma
+    return A
+
+
+def init_torch(m: int, n: int, r: int, seed: int, device="cuda"):
+    """U0 (m x r) then V0^T (n x r), i.i.d. Uniform[0, 1), FP32, drawn with
+    PyTorch's generator on `device`."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    U0 = torch.rand(m, r, generator=g, device=device)
+    V0 = torch.rand(r, n, generator=g, device=device)
+    return U0, V0.t().contiguous()
