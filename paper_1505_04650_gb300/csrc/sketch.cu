@@ -318,7 +318,7 @@ size_t prod_workspace(int64_t m, int64_t n, int k, cnmf_dtype a_type) {
   // two partial tiles per CTA; at most 4 resident CTAs per SM.
   size_t w = a_type == CNMF_F64 ? 8 : 4;
   size_t b = (size_t)4 * num_sms() * 2 * SK_BP * prod_kp(k) * w + 256;
-  if (a_type == CNMF_BF16) b = std::max(b, tc_workspace(m, n, k));
+  if (a_type != CNMF_F64) b = std::max(b, tc_workspace(m, n, k));
   return b;
 }
 
@@ -357,7 +357,7 @@ cnmf_status launch_prod(const ProdArgs& a, void* ws, size_t ws_bytes,
                         cudaStream_t s) {
   if (ws_bytes < prod_workspace(a.m, a.n, std::max(a.kb, a.kz), a.a_type))
     return CNMF_E_WORKSPACE;
-  if (a.a_type == CNMF_BF16 && !tc_disabled() && tc_applicable(a))
+  if (a.a_type != CNMF_F64 && !tc_disabled() && tc_applicable(a))
     return launch_prod_tc(a, ws, a.status, s);
   if (a.a_type == CNMF_F64)
     return a.trans ? dispatch_kp<double, double, true>(a, ws, s)

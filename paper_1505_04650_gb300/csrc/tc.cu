@@ -1,21 +1,29 @@
-// Tensor-core products with a BF16-stored A (the mixed-precision sketch of
-// the compression, Alg. 1 power scheme on A and A^T):
+// Tensor-core products with A (the sketch products of the compression,
+// Alg. 1 power scheme on A and A^T), for BF16- and FP32-stored A:
 //
 //   Z = A B    (output rows i of A; A tile K-major)           trans = false
 //   Z = A^T B  (output rows j = columns of A; A tile MN-major) trans = true
 //
-// B (FP32, S x k) is first packed into bf16 "hi | lo" planes, transposed so
-// that the reduction index is contiguous: Bp[c][s] = bf16(B[s][c]) and
-// Bp[KP + c][s] = bf16(B[s][c] - hi) (|B - hi - lo| <= 2^-18 |B|).  One MMA
-// with N = 2 KP then yields A B_hi and A B_lo side by side in TMEM; the
-// epilogue adds the two halves in FP32.  A is read exactly as stored.
+// B (FP32, S x k) is first packed into "hi | lo" planes, transposed so that
+// the reduction index is contiguous: Bp[c][s] = hi(B[s][c]) and Bp[KP + c][s]
+// = lo = B[s][c] - hi.  One MMA with N = 2 KP yields A B_hi and A B_lo side
+// by side in TMEM; the epilogue adds the two halves in FP32.
+//  * BF16 A (kind::f16): hi, lo are bf16 (|B - hi - lo| <= 2^-18 |B|); A is
+//    used exactly as stored.
+//  * FP32 A (kind::tf32, 3xTF32 split): hi = B rounded to TF32, lo = the FP32
+//    remainder.  The tensor core reads A truncated to TF32 (A_hi); two
+//    converter warps write A_lo = A - A_hi into a second shared-memory tile
+//    and a second MMA adds A_lo B_hi into the hi half.  The dropped terms
+//    (A_lo B_lo and the TF32 truncation of the lo parts) are about 2^-20 of
+//    |A||B|.
 //
 // Kernel (one CTA per SM, persistent, stream-K split of (output tile,
-// 64-wide reduction chunk) units like the CUDA-core kernel, sharing its
+// 128-byte reduction chunk) units like the CUDA-core kernel, sharing its
 // fix-up): warp 0 lane 0 issues TMA loads (128-byte swizzle) into an
 // N-stage mbarrier ring; warp 1 allocates TMEM and lane 0 issues
-// tcgen05.mma (M = 128, N = 2 KP, K = 16, FP32 accumulate) into one of two
-// TMEM accumulators; warps 4-7 drain finished accumulators with
+// tcgen05.mma (M = 128, N = 2 KP, K = 16 bf16 / 8 tf32, FP32 accumulate)
+// into one of two TMEM accumulators; for FP32 A, warps 2-3 produce A_lo per
+// stage; warps 4-7 drain finished accumulators with
 // tcgen05.ld and write FP32 rows (or split-tile partials).  Every wait is
 // bounded: on expiry the kernel records CNMF_E_TIMEOUT, drains its own
 // copies and MMAs (bounded), frees TMEM and returns.
@@ -31,21 +39,34 @@
 namespace cnmf {
 
 constexpr int TC_BM = 128;   // output rows per tile (MMA M)
-constexpr int TC_BK = 64;    // reduction elements per stage (128 B of bf16)
-constexpr int TC_NT = 256;   // warp 0 TMA, warp 1 MMA, warps 4-7 epilogue
 
-template <int KP>
+// Warp roles: 0 TMA, 1 MMA, 2-3 A_lo into shared memory (FP32, A K-major),
+// 4-7 epilogue, 8-11 A_hi / A_lo into tensor memory (FP32, A MN-major).
+template <int KP, bool F32, bool TRANS>
 struct TcCfg {
+  static constexpr bool TMEM_A = F32 && TRANS;      // A operand from TMEM
+  static constexpr int NT = TMEM_A ? 384 : 256;
+  static constexpr int ESZ = F32 ? 4 : 2;           // bytes per A / B element
+  static constexpr int BK = 128 / ESZ;              // reduction per stage
   static constexpr int N = 2 * KP;
-  static constexpr int A_BYTES = TC_BM * TC_BK * 2;   // 16 KiB
-  static constexpr int B_BYTES = N * TC_BK * 2;        // N rows x 128 B
-  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int A_BYTES = TC_BM * 128;       // 16 KiB
+  static constexpr int ALO_BYTES = (F32 && !TRANS) ? A_BYTES : 0;
+  static constexpr int B_BYTES = N * 128;           // N rows x 128 B
+  static constexpr int STAGE = A_BYTES + ALO_BYTES + B_BYTES;
   static constexpr int ST_FIT = (200 * 1024) / STAGE;
-  static constexpr int STAGES = ST_FIT > 8 ? 8 : ST_FIT;
-  static constexpr int TMEM_COLS = 2 * N <= 64 ? 64
-                                   : 2 * N <= 128 ? 128
-                                   : 2 * N <= 256 ? 256 : 512;
+  // TMEM: NACC accumulators of N columns, then (TMEM_A) per stage BK
+  // columns of A_hi and BK of A_lo.
+  static constexpr int NACC = (!TMEM_A || 512 - 2 * N >= 3 * 2 * BK) ? 2 : 1;
+  static constexpr int ST_TMEM = TMEM_A ? (512 - NACC * N) / (2 * BK) : 8;
+  static constexpr int ST_A = ST_FIT < ST_TMEM ? ST_FIT : ST_TMEM;
+  static constexpr int STAGES = ST_A > 8 ? 8 : ST_A;
+  static constexpr int TMEM_COLS = TMEM_A ? 512
+                                   : NACC * N <= 64 ? 64
+                                   : NACC * N <= 128 ? 128
+                                   : NACC * N <= 256 ? 256 : 512;
+  static constexpr int A_TMEM = NACC * N;           // first A column
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE;
+  static_assert(STAGES >= 2, "pipeline needs two stages");
 };
 
 // ---------------------------------------------------------------------------
@@ -154,10 +175,53 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo,
   d |= (uint64_t)2 << 61;
   return d;
 }
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, B K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: D FP32; A, B both BF16 (kind::f16, format 1) or
+// both TF32 (kind::tf32, format 2); B K-major; A K- or MN-major.
+__host__ __device__ constexpr uint32_t idesc_mk(int M, int N, bool a_mn,
+                                               bool tf32) {
+  return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
+         ((a_mn ? 1u : 0u) << 15) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma_tf32(uint32_t dtm, uint64_t ad,
+                                            uint64_t bd, uint32_t idesc,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtm),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// A operand in tensor memory (K-major by construction).
+__device__ __forceinline__ void tc_mma_tf32_ta(uint32_t dtm, uint32_t atm,
+                                               uint64_t bd, uint32_t idesc,
+                                               uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+          dtm),
+      "r"(atm), "l"(bd), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// 32 lanes x 32 columns of 32-bit words from registers into TMEM.
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t v[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, "
+      "%7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, "
+      "%22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+      "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
+      "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]),
+      "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]),
+      "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 __host__ __device__ __forceinline__ int64_t tc_split_start(int64_t c, int64_t U,
@@ -166,11 +230,13 @@ __host__ __device__ __forceinline__ int64_t tc_split_start(int64_t c, int64_t U,
 }
 
 // ---------------------------------------------------------------------------
-// B (S x kb, FP32, pitch ldb) -> Bp (2 KP x spad, bf16), transposed hi | lo.
+// B (S x kb, FP32, pitch ldb) -> Bp (2 KP x spad, bf16 or TF32-valued FP32),
+// transposed hi | lo.
 // ---------------------------------------------------------------------------
+template <bool F32>
 __global__ void k_pack_panel(const float* __restrict__ B, int64_t S,
                              int64_t ldb, int kb, int KP,
-                             bf16* __restrict__ Bp, int64_t spad) {
+                             void* __restrict__ Bpv, int64_t spad) {
   __shared__ float tile[32][33];
   const int64_t s0 = (int64_t)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -186,29 +252,47 @@ __global__ void k_pack_panel(const float* __restrict__ B, int64_t S,
     const int64_t s = s0 + tx;
     if (c >= KP || s >= spad) continue;
     const float v = tile[tx][cc];
-    const bf16 hi = __float2bfloat16_rn(v);
-    const bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    Bp[(int64_t)c * spad + s] = hi;
-    Bp[(int64_t)(KP + c) * spad + s] = lo;
+    if (F32) {
+      float* Bp = reinterpret_cast<float*>(Bpv);
+      const float hi = tf32_rna(v);
+      Bp[(int64_t)c * spad + s] = hi;
+      Bp[(int64_t)(KP + c) * spad + s] = tf32_rna(v - hi);
+    } else {
+      bf16* Bp = reinterpret_cast<bf16*>(Bpv);
+      const bf16 hi = __float2bfloat16_rn(v);
+      Bp[(int64_t)c * spad + s] = hi;
+      Bp[(int64_t)(KP + c) * spad + s] =
+          __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // The product kernel
 // ---------------------------------------------------------------------------
-template <int KP, bool TRANS>
-__global__ void __launch_bounds__(TC_NT, 1)
+template <int KP, bool TRANS, bool F32>
+__global__ void __launch_bounds__((TcCfg<KP, F32, TRANS>::NT), 1)
     k_tc_prod(const __grid_constant__ CUtensorMap tmA,
               const __grid_constant__ CUtensorMap tmB, int64_t P,
               float* __restrict__ Z, int64_t ldz, int kz,
               float* __restrict__ part, int64_t U, int64_t chunks,
               int32_t* status) {
-  typedef TcCfg<KP> C;
+  typedef TcCfg<KP, F32, TRANS> C;
   constexpr int N = C::N;
   constexpr int ST = C::STAGES;
-  constexpr uint32_t IDESC = idesc_bf16(TC_BM, N, TRANS);
+  constexpr int NACC = C::NACC;
+  constexpr bool TMEM_A = C::TMEM_A;
+  constexpr int BK = C::BK;
+  constexpr int MMA_K = F32 ? 8 : 16;                // reduction per MMA
+  // A from TMEM is K-major; from shared memory K-major unless TRANS
+  constexpr bool A_MN = TRANS && !TMEM_A;
+  constexpr uint32_t IDESC = idesc_mk(TC_BM, N, A_MN, F32);
+  constexpr uint32_t IDESC_HI = idesc_mk(TC_BM, KP, A_MN, F32);
+  // MN-major A: one TMA box per 128-byte chunk of the MN index
+  constexpr int MN_CHUNK = 128 / C::ESZ;             // 64 bf16 / 32 fp32
+  constexpr int BOX_BYTES = MN_CHUNK * BK * C::ESZ;  // bytes of one box
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[8], empty_bar[8];
+  __shared__ __align__(8) uint64_t full_bar[8], empty_bar[8], lo_bar[8];
   __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
@@ -223,6 +307,7 @@ __global__ void __launch_bounds__(TC_NT, 1)
     for (int i = 0; i < ST; ++i) {
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], 1);
+      mbar_init(&lo_bar[i], TMEM_A ? 4 : 2);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accf_bar[i], 1);
@@ -265,18 +350,19 @@ __global__ void __launch_bounds__(TC_NT, 1)
           break;
         }
         unsigned char* sa = smem + (size_t)stage * C::STAGE;
-        unsigned char* sb = sa + C::A_BYTES;
-        mbar_expect_tx(&full_bar[stage], (uint32_t)C::STAGE);
+        unsigned char* sb = sa + C::A_BYTES + C::ALO_BYTES;
+        mbar_expect_tx(&full_bar[stage], (uint32_t)(C::A_BYTES + C::B_BYTES));
         if (!TRANS) {
-          tma_load_2d(sa, &tmA, (int)(ts * TC_BK), (int)(tp * TC_BM),
+          tma_load_2d(sa, &tmA, (int)(ts * BK), (int)(tp * TC_BM),
                       &full_bar[stage]);
         } else {
-          tma_load_2d(sa, &tmA, (int)(tp * TC_BM), (int)(ts * TC_BK),
-                      &full_bar[stage]);
-          tma_load_2d(sa + C::A_BYTES / 2, &tmA, (int)(tp * TC_BM + 64),
-                      (int)(ts * TC_BK), &full_bar[stage]);
+#pragma unroll
+          for (int b = 0; b < TC_BM / MN_CHUNK; ++b)
+            tma_load_2d(sa + b * BOX_BYTES, &tmA,
+                        (int)(tp * TC_BM + b * MN_CHUNK), (int)(ts * BK),
+                        &full_bar[stage]);
         }
-        tma_load_2d(sb, &tmB, (int)(ts * TC_BK), 0, &full_bar[stage]);
+        tma_load_2d(sb, &tmB, (int)(ts * BK), 0, &full_bar[stage]);
         issued[stage] = true;
         issued_phase[stage] = phase;
         if (++stage == ST) { stage = 0; phase ^= 1u; }
@@ -309,28 +395,55 @@ __global__ void __launch_bounds__(TC_NT, 1)
       tc_fence_after();
       const uint32_t dtm = tmem + (uint32_t)(ab * N);
       for (int64_t ts = ts0; ts < ts1; ++ts) {
-        if (!mbar_wait(&full_bar[stage], phase, &abort_s, status)) {
+        if (!mbar_wait(&full_bar[stage], phase, &abort_s, status) ||
+            (F32 && !mbar_wait(&lo_bar[stage], phase, &abort_s, status))) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + (size_t)stage * C::STAGE);
-        const uint32_t sb = sa + C::A_BYTES;
+        const uint32_t sb = sa + C::A_BYTES + C::ALO_BYTES;
+        if (TMEM_A) {
+          // A_hi . [B_hi | B_lo], then A_lo . B_hi, A from this stage's
+          // TMEM columns
+          const uint32_t ahi = tmem + (uint32_t)(C::A_TMEM + stage * 2 * BK);
 #pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          uint64_t ad, bd;
-          if (!TRANS) ad = sdesc(sa + kk * 32, 16, 1024);          // K-major
-          else ad = sdesc(sa + kk * 2048, C::A_BYTES / 2, 1024);   // MN-major
-          bd = sdesc(sb + kk * 32, 16, 1024);
-          tc_mma(dtm, ad, bd, IDESC, (ts > ts0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < BK / MMA_K; ++kk)
+            tc_mma_tf32_ta(dtm, ahi + kk * MMA_K, sdesc(sb + kk * 32, 16, 1024),
+                           IDESC, (ts > ts0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+          for (int kk = 0; kk < BK / MMA_K; ++kk)
+            tc_mma_tf32_ta(dtm, ahi + BK + kk * MMA_K,
+                           sdesc(sb + kk * 32, 16, 1024), IDESC_HI, 1u);
           any = true;
+        } else {
+#pragma unroll
+        for (int kk = 0; kk < BK / MMA_K; ++kk) {
+          // K-major: the next MMA_K elements sit 32 bytes further along the
+          // swizzled row; MN-major: MMA_K rows of 128 bytes further.
+          const uint64_t ad =
+              !TRANS ? sdesc(sa + kk * 32, 16, 1024)
+                     : sdesc(sa + kk * MMA_K * 128, BOX_BYTES, 1024);
+          const uint64_t bd = sdesc(sb + kk * 32, 16, 1024);
+          const uint32_t acc = (ts > ts0 || kk > 0) ? 1u : 0u;
+          if (F32) tc_mma_tf32(dtm, ad, bd, IDESC, acc);
+          else tc_mma(dtm, ad, bd, IDESC, acc);
+          any = true;
+        }
+        if (F32) {   // A_lo . B_hi into the hi half (A K-major here)
+          const uint32_t sl = sa + C::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / MMA_K; ++kk)
+            tc_mma_tf32(dtm, sdesc(sl + kk * 32, 16, 1024),
+                        sdesc(sb + kk * 32, 16, 1024), IDESC_HI, 1u);
+        }
         }
         tc_commit(&empty_bar[stage]);
         if (++stage == ST) { stage = 0; phase ^= 1u; }
       }
       if (!ok) break;
       tc_commit(&accf_bar[ab]);
-      if (++ab == 2) { ab = 0; aphase ^= 1u; }
+      if (++ab == NACC) { ab = 0; aphase ^= 1u; }
       u = tp * chunks + ts1;
     }
     if (any) {   // all MMAs complete before TMEM is released
@@ -339,7 +452,87 @@ __global__ void __launch_bounds__(TC_NT, 1)
       while (!mbar_try(&drain_bar, 0) && globaltimer_ns() - t0 < 2000000000ull) {
       }
     }
-  } else if (warp >= 4) {
+  } else if (F32 && !TRANS && (warp == 2 || warp == 3)) {
+    // ---------------- A_lo converter (FP32 A) ----------------
+    // The tensor core reads an FP32 operand as TF32 (the low 13 mantissa
+    // bits ignored); A_lo = A - that value is exact in FP32.  Element-wise
+    // in the same (swizzled) layout, so MN- and K-major tiles alike.
+    const int t = threadIdx.x - 64;
+    int stage = 0;
+    uint32_t phase = 0;
+    int64_t u = u0;
+    bool ok = true;
+    while (ok && u < u1) {
+      const int64_t tp = u / chunks, ts0 = u % chunks;
+      const int64_t ts1 = min(chunks, ts0 + (u1 - u));
+      for (int64_t ts = ts0; ts < ts1; ++ts) {
+        if (!mbar_wait(&full_bar[stage], phase, &abort_s, status)) {
+          ok = false;
+          break;
+        }
+        const float4* src = reinterpret_cast<const float4*>(
+            smem + (size_t)stage * C::STAGE);
+        float4* dst = reinterpret_cast<float4*>(
+            smem + (size_t)stage * C::STAGE + C::A_BYTES);
+#pragma unroll 4
+        for (int i = t; i < C::A_BYTES / 16; i += 64) {
+          float4 v = src[i];
+          v.x -= __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+          v.y -= __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+          v.z -= __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+          v.w -= __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          dst[i] = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&lo_bar[stage]);
+        if (++stage == ST) { stage = 0; phase ^= 1u; }
+      }
+      u = tp * chunks + ts1;
+    }
+  } else if (TMEM_A && warp >= 8) {
+    // ---------------- A_hi / A_lo into TMEM (FP32 A, MN-major tile) -------
+    // Warp 8 + w owns TMEM lanes 32 w .. 32 w + 31, i.e. output rows j of
+    // TMA box w.  Lane l reads column j = 32 w + l of the tile (row i of the
+    // box is 128 bytes, 16-byte chunks swizzled by i mod 8), so TMEM lane j
+    // gets row j of A^T: K-major.  A_hi is the FP32 value itself (the tensor
+    // core ignores the low 13 mantissa bits), A_lo = A - A_hi exactly.
+    const int w = warp - 8;
+    int stage = 0;
+    uint32_t phase = 0;
+    int64_t u = u0;
+    bool ok = true;
+    while (ok && u < u1) {
+      const int64_t tp = u / chunks, ts0 = u % chunks;
+      const int64_t ts1 = min(chunks, ts0 + (u1 - u));
+      for (int64_t ts = ts0; ts < ts1; ++ts) {
+        if (!mbar_wait(&full_bar[stage], phase, &abort_s, status)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* box = smem + (size_t)stage * C::STAGE +
+                                   w * BOX_BYTES + (lane & 3) * 4;
+        uint32_t hi[32], lo[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float v = *reinterpret_cast<const float*>(
+              box + i * 128 + ((((lane >> 2) ^ i) & 7) << 4));
+          hi[i] = __float_as_uint(v);
+          lo[i] = __float_as_uint(v - __uint_as_float(hi[i] & 0xFFFFE000u));
+        }
+        const uint32_t ta = tmem + ((uint32_t)(32 * w) << 16) +
+                            (uint32_t)(C::A_TMEM + stage * 2 * BK);
+        tc_st32(ta, hi);
+        tc_st32(ta + BK, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&lo_bar[stage]);
+        if (++stage == ST) { stage = 0; phase ^= 1u; }
+      }
+      u = tp * chunks + ts1;
+    }
+  } else if (warp >= 4 && warp < 8) {
     // ---------------- epilogue ----------------
     const int q = warp - 4;                 // TMEM lane quarter
     const int row = 32 * q + lane;
@@ -373,7 +566,7 @@ __global__ void __launch_bounds__(TC_NT, 1)
       }
       tc_fence_before();
       mbar_arrive(&acce_bar[ab]);
-      if (++ab == 2) { ab = 0; aphase ^= 1u; }
+      if (++ab == NACC) { ab = 0; aphase ^= 1u; }
       first = false;
       u = tp * chunks + ts1;
     }
@@ -409,48 +602,53 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   return fn;
 }
 
-static bool make_map(CUtensorMap* m, const void* base, uint64_t inner,
-                     uint64_t outer, uint64_t row_bytes, uint32_t box_inner,
-                     uint32_t box_outer) {
+static bool make_map(CUtensorMap* m, const void* base, bool f32,
+                     uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                     uint32_t box_inner, uint32_t box_outer) {
   auto enc = tmap_encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {row_bytes};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
-             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+             2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static int tc_kp(int k) { return pad_k(k); }
 
 size_t tc_workspace(int64_t m, int64_t n, int k) {
+  // split-tile partials, then the packed B panel (4 bytes per element covers
+  // both the bf16 and the TF32 packing)
   const int KP = tc_kp(k);
   const int64_t spad = (std::max(m, n) + 7) / 8 * 8;
   size_t b = 0;
   b += (((size_t)num_sms() * 2 * TC_BM * KP * 4) + 255) & ~size_t(255);
-  b += (((size_t)2 * KP * spad * 2) + 255) & ~size_t(255);
+  b += (((size_t)2 * KP * spad * 4) + 255) & ~size_t(255);
   return b + 256;
 }
 
 bool tc_applicable(const ProdArgs& a) {
-  if (a.a_type != CNMF_BF16) return false;
-  if ((uintptr_t)a.A % 16 != 0 || (a.lda * 2) % 16 != 0) return false;
+  if (a.a_type != CNMF_BF16 && a.a_type != CNMF_F32) return false;
+  const int64_t es = a.a_type == CNMF_F32 ? 4 : 2;
+  if ((uintptr_t)a.A % 16 != 0 || (a.lda * es) % 16 != 0) return false;
   if (std::max(a.kb, a.kz) > 128 || a.m < 1 || a.n < 1) return false;
   if (a.m >= (1ll << 31) || a.n >= (1ll << 31)) return false;
   return tmap_encoder() != nullptr;
 }
 
-template <int KP, bool TRANS>
+template <int KP, bool TRANS, bool F32>
 static cnmf_status run_tc(const ProdArgs& a, void* ws, int32_t* status,
                           cudaStream_t s) {
-  typedef TcCfg<KP> C;
+  typedef TcCfg<KP, F32, TRANS> C;
   static std::once_flag once;
   static bool smem_ok = false;
   std::call_once(once, [] {
-    smem_ok = set_max_smem((const void*)k_tc_prod<KP, TRANS>, C::SMEM);
+    smem_ok = set_max_smem((const void*)k_tc_prod<KP, TRANS, F32>, C::SMEM);
   });
   if (!smem_ok) return CNMF_E_INVALID_ARG;
   const int64_t P = TRANS ? a.n : a.m;
@@ -458,28 +656,29 @@ static cnmf_status run_tc(const ProdArgs& a, void* ws, int32_t* status,
   const int64_t spad = (S + 7) / 8 * 8;
   Carve cv(ws, SIZE_MAX);
   float* part = cv.take<float>((size_t)num_sms() * 2 * TC_BM * KP);
-  bf16* Bp = cv.take<bf16>((size_t)2 * KP * spad);
+  void* Bp = cv.take<char>((size_t)2 * KP * spad * C::ESZ);
   // pack B
   dim3 pg((unsigned)ceil_div(spad, 32), (unsigned)ceil_div(KP, 32));
-  k_pack_panel<<<pg, 256, 0, s>>>((const float*)a.B, S, a.ldb, a.kb, KP, Bp,
-                                  spad);
+  k_pack_panel<F32><<<pg, 256, 0, s>>>((const float*)a.B, S, a.ldb, a.kb, KP,
+                                       Bp, spad);
   CNMF_CHECK_LAUNCH();
   CUtensorMap ta, tb;
   bool ok;
+  constexpr int MN_CHUNK = 128 / C::ESZ;
   if (!TRANS)
-    ok = make_map(&ta, a.A, (uint64_t)a.n, (uint64_t)a.m, (uint64_t)a.lda * 2,
-                  TC_BK, TC_BM);
+    ok = make_map(&ta, a.A, F32, (uint64_t)a.n, (uint64_t)a.m,
+                  (uint64_t)a.lda * C::ESZ, C::BK, TC_BM);
   else
-    ok = make_map(&ta, a.A, (uint64_t)a.n, (uint64_t)a.m, (uint64_t)a.lda * 2,
-                  64, TC_BK);
-  ok = ok && make_map(&tb, Bp, (uint64_t)spad, (uint64_t)(2 * KP),
-                      (uint64_t)spad * 2, TC_BK, 2 * KP);
+    ok = make_map(&ta, a.A, F32, (uint64_t)a.n, (uint64_t)a.m,
+                  (uint64_t)a.lda * C::ESZ, MN_CHUNK, C::BK);
+  ok = ok && make_map(&tb, Bp, F32, (uint64_t)spad, (uint64_t)(2 * KP),
+                      (uint64_t)spad * C::ESZ, C::BK, 2 * KP);
   if (!ok) return CNMF_E_INVALID_ARG;
   const int64_t tiles = ceil_div(P, TC_BM);
-  const int64_t chunks = std::max<int64_t>(1, ceil_div(S, TC_BK));
+  const int64_t chunks = std::max<int64_t>(1, ceil_div(S, C::BK));
   const int64_t U = tiles * chunks;
   const int64_t G = std::min<int64_t>(U, num_sms());
-  k_tc_prod<KP, TRANS><<<(unsigned)G, TC_NT, C::SMEM, s>>>(
+  k_tc_prod<KP, TRANS, F32><<<(unsigned)G, C::NT, C::SMEM, s>>>(
       ta, tb, P, (float*)a.Z, a.ldz, a.kz, part, U, chunks, status);
   CNMF_CHECK_LAUNCH();
   if (chunks > 1)
@@ -491,10 +690,14 @@ static cnmf_status run_tc(const ProdArgs& a, void* ws, int32_t* status,
 cnmf_status launch_prod_tc(const ProdArgs& a, void* ws, int32_t* status,
                            cudaStream_t s) {
   const int KP = tc_kp(std::max(a.kb, a.kz));
-#define TC_CASE(K)                                                  \
-  case K:                                                           \
-    return a.trans ? run_tc<K, true>(a, ws, status, s)              \
-                   : run_tc<K, false>(a, ws, status, s);
+  const bool f32 = a.a_type == CNMF_F32;
+#define TC_CASE(K)                                                        \
+  case K:                                                                 \
+    if (f32)                                                              \
+      return a.trans ? run_tc<K, true, true>(a, ws, status, s)            \
+                     : run_tc<K, false, true>(a, ws, status, s);          \
+    return a.trans ? run_tc<K, true, false>(a, ws, status, s)             \
+                   : run_tc<K, false, false>(a, ws, status, s);
   switch (KP) {
     TC_CASE(16)
     TC_CASE(32)

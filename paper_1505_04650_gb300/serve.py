@@ -268,7 +268,7 @@ class Server:
                 outs = []
                 for rq in finished:
                     outs.append(cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt))
-                torch.cuda.synchronize(self.dev)
+                self.main.synchronize()   # this round only; compressions go on
                 now = clock()
                 for rq, res in zip(finished, outs):
                     rq.t_done = now
@@ -277,7 +277,7 @@ class Server:
                     in_use -= rq.nbytes
                     done.append(rq)
             elif compressing:
-                torch.cuda.synchronize(self.dev)
+                compressing[0].event.synchronize()
             elif pending and realtime:
                 time.sleep(max(0.0, min(0.001, pending[0].t_arrive - clock())))
         raise_on_status(self.status, "serving")

@@ -3,8 +3,10 @@
 Every call goes through the C ABI (ctypes binding).  Tolerances:
 * integer work (Philox words, anchors): bit-exact;
 * products with A: the componentwise rounding bound of a length-s dot
-  product, |Z - Z_exact| <= (s + 2) u (|A| |X|), u = 2^-24 (FP32 / BF16
-  storage) or 2^-53 (FP64) -- holds at any size;
+  product, |Z - Z_exact| <= (s + 2) u (|A| |X|), u = 2^-53 (FP64); FP32 and
+  BF16 A run on the tensor cores with FP32 accumulation (2u per add, u =
+  2^-24) plus the operand-split residual (bf16 hi + lo of X: 2^-17; 3xTF32:
+  2^-19) -- holds at any size;
 * orthonormal bases: unique thin Q (positive diag R) elementwise, with a
   tolerance scaled by u and the panel's condition number.
 """
@@ -45,9 +47,20 @@ def test_gaussian_matches_oracle(dtype):
             assert np.abs(z - ref).max() <= 2 * 2.0 ** -24 * np.abs(ref).max()
 
 
-CASES = [  # m, n, k
+CASES = [  # m, n, k  (n % 4 == 0: FP32 rows 16-byte aligned, tensor cores)
     (1, 1, 1), (37, 53, 5), (300, 257, 30), (129, 4100, 16), (5000, 33, 20),
-    (640, 700, 60), (200, 300, 80), (150, 170, 128)]
+    (640, 700, 60), (200, 300, 80), (150, 170, 128), (1000, 1028, 30),
+    (257, 516, 128), (4100, 260, 48), (3, 8, 2)]
+
+
+def product_bound(storage, s):
+    """(per-add factor, split residual) of the product kernels' bound."""
+    u = unit(storage)
+    if storage == "bf16":
+        return (s + 2) * 2 * u + 2.0 ** -17
+    if storage == "f32":
+        return (s + 2) * 2 * u + 2.0 ** -19
+    return (s + 2) * u
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
@@ -71,14 +84,10 @@ def test_sketch_pass_products(storage, m, n, k):
     Zm, Zn = cn.cnmf_sketch_pass(Ad, Xd, Yd, status=st)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
-    u = unit(storage)
-    # BF16 A runs on the tensor cores: FP32 accumulation (allow 2u per add)
-    # plus the 2^-18 residual of the bf16 hi + lo split of X / Y
-    acc, split = (2 * u, 2.0 ** -17) if storage == "bf16" else (u, 0.0)
     ref_m = Aw @ X
-    bnd_m = ((n + 2) * acc + split) * (np.abs(Aw) @ np.abs(X))
+    bnd_m = product_bound(storage, n) * (np.abs(Aw) @ np.abs(X))
     ref_n = Aw.T @ Y
-    bnd_n = ((m + 2) * acc + split) * (np.abs(Aw).T @ np.abs(Y))
+    bnd_n = product_bound(storage, m) * (np.abs(Aw).T @ np.abs(Y))
     assert np.all(np.abs(to_np(Zm) - ref_m) <= bnd_m + 1e-300)
     assert np.all(np.abs(to_np(Zn) - ref_n) <= bnd_n + 1e-300)
 
@@ -93,7 +102,7 @@ def test_sketch_pass_pitched_and_one_sided():
     X = np.random.default_rng(1).standard_normal((n, k)).astype(np.float32)
     Zm, Zn = cn.cnmf_sketch_pass(Ad, torch.tensor(X).cuda(), None)
     assert Zn is None
-    bnd = (n + 2) * 2.0 ** -24 * (np.abs(A) @ np.abs(X.astype(np.float64)))
+    bnd = product_bound("f32", n) * (np.abs(A) @ np.abs(X.astype(np.float64)))
     assert np.all(np.abs(to_np(Zm) - A @ X) <= bnd)
 
 
