@@ -185,7 +185,10 @@ cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type, int64_t m,
  *   Vt  in/out n x r (V^T).  On a fresh start: the initial V^T.
  *   state  in/out, cnmf_factor_state_bytes() bytes, W-typed sections in
  *          this order: Lam (m x r), Phit (n x r), Yt (r x d), Xt (d x r),
- *          then int64 k (sweeps done so far) at the next 8-byte boundary.
+ *          then int64 k (sweeps done so far) at the next 8-byte boundary,
+ *          then Zx, Zy (r x r each): -(Yt Yt^T + lam I)^-1 and
+ *          -(Xt^T Xt + phi I)^-1 of the last sweep, from which the next
+ *          sweep's inverses are refined (valid when k > 0).
  *          resume = 0: Yt <- V R^T, Lam = Phi = 0, k = 0 (Alg. 4 setup).
  *          resume = 1: continue from the state; the result is bitwise the
  *          same as an uninterrupted run.

@@ -211,7 +211,15 @@ class FactorState:
             cnt = shp[0] * shp[1]
             out[name] = self.buf[off:off + cnt * e].view(self.dtype).view(*shp)
             off += cnt * e
-        out["k"] = self.buf[self.buf.numel() - 8:].view(torch.int64)
+        if self.d:
+            # int64 k at the next 8-byte boundary, then the two kept r x r
+            # inverses of the ADMM solves
+            off = (off + 7) // 8 * 8
+            out["k"] = self.buf[off:off + 8].view(torch.int64)
+            out["Z"] = self.buf[off + 8:off + 8 + 2 * r * r * e] \
+                .view(self.dtype).view(2, r, r)
+        else:
+            out["k"] = self.buf[self.buf.numel() - 8:].view(torch.int64)
         return out
 
     def __getattr__(self, name):

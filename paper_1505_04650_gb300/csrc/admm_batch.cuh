@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(AD_NT)
       (((size_t)a.m * r + (size_t)a.n * r + 2 * (size_t)r * d) * sizeof(W) + 7) &
       ~size_t(7);
   a.kcount = (int64_t*)(st + sbytes);
+  a.Zs = (W*)(st + sbytes + 8);
   W* keep = (W*)it.scratch;                        // reduced SX | SY^T
   a.SX = keep; a.SY = keep + dr;
   a.status = status;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(AD_NT)
   };
 
   int parity = 0;
+  bool have = false;
   if (it.flags & CNMF_BATCH_FRESH) {
     sweep_fast<W, DMAX, false>(a, sm, o, 0, nullptr, CS, rank,
                                sm + b.share0);
@@ -109,10 +111,14 @@ __global__ void __launch_bounds__(AD_NT)
       const int k = e / r, bb = e % r;
       sm[o.YtT + k * RP + bb] = a.Yt[bb * d + k];
     }
+    // the inverses the last launch kept (a problem's sweeps may be split
+    // over launches with the arithmetic of one run)
+    have = *a.kcount > 0;
+    if (have) load_inverses<W>(a.Zs, r, RP, sm + o.Zx, sm + o.Zy);
     __syncthreads();
   }
   for (int s = 0; s < sweeps; ++s) {
-    small_fast<W, RMAX>(a, sm, o, nullptr, SXs, SYs, true);
+    small_fast<W, RMAX>(a, sm, o, have || s > 0, nullptr, SXs, SYs, true);
     const int buf = parity ? b.share1 : b.share0;
     sweep_fast<W, DMAX, false>(a, sm, o, 2, nullptr, CS, rank, sm + buf);
     reduce(buf, 2 * dr);
@@ -127,6 +133,7 @@ __global__ void __launch_bounds__(AD_NT)
       keep[e] = SXs[e];
       keep[dr + e] = SYs[e];
     }
+    if (sweeps > 0) store_inverses<W>(a.Zs, r, RP, sm + o.Zx, sm + o.Zy);
     if (threadIdx.x == 0) *a.kcount += sweeps;
   }
 }

@@ -14,17 +14,19 @@
 //
 // One small-algebra step is six block-wide phases:
 //   M  = SX + At Yt^T            G = Yt Yt^T + lam I        (one phase)
-//   G <- -G^-1                                              (sweep operator)
+//   Zx <- -G^-1     (Newton-Schulz from the last sweep's Zx, else the sweep
+//                    operator)
 //   Xt = M (Yt Yt^T + lam I)^-1
 //   M  = SY^T + At^T Xt          G = Xt^T Xt + phi I        (one phase)
-//   G <- -G^-1
+//   Zy <- -G^-1
 //   Yt^T = M (Xt^T Xt + phi I)^-1    (= (G^-1 MY)^T, G symmetric)
 // Each output quad C[p][4q..4q+3] is one thread's task: a length-S loop of
 // one scalar load, one 16-byte load and four FMAs.
 
 struct FastSmem {
   int RP, dp, nl;
-  int At, YtT, Xt, M, G, v, Red, sL, sU, sLam, sRt, sVt, sPhit, total;
+  int At, YtT, Xt, M, G, Zx, Zy, E, F, v, Red, sL, sU, sLam, sRt, sVt, sPhit,
+      total;
   // dmax: the register tile width; resident rows are stored zero-padded to
   // dmax with pitch dmax + 4 (4 banks apart: the <= 8 rows one warp reads
   // with 16-byte loads hit distinct banks).
@@ -40,6 +42,10 @@ struct FastSmem {
     Xt = take(d * RP);
     M = take(d * RP);
     G = take(r * RP);
+    Zx = take(r * RP);
+    Zy = take(r * RP);
+    E = take(r * RP);
+    F = take(r * RP);
     v = take(2 * 32);
     Red = take((int64_t)nl * d * r);
     sL = res ? take(mu * dp) : 0;
@@ -160,12 +166,86 @@ __device__ void fast_sweep_inverse(W* G, W* vbuf, int r, int RP,
   __syncthreads();
 }
 
+// The two kept inverses in the factor state: Zx then Zy, r x r each.
+template <typename W>
+__device__ void load_inverses(const W* Zs, int r, int RP, W* Zx, W* Zy) {
+  for (int e = threadIdx.x; e < r * RP; e += AD_NT) {
+    const int i = e / RP, k = e % RP;
+    Zx[e] = k < r ? __ldcg(Zs + i * r + k) : W(0);
+    Zy[e] = k < r ? __ldcg(Zs + r * r + i * r + k) : W(0);
+  }
+}
+template <typename W>
+__device__ void store_inverses(W* Zs, int r, int RP, const W* Zx,
+                               const W* Zy) {
+  for (int e = threadIdx.x; e < r * r; e += AD_NT) {
+    const int i = e / r, k = e % r;
+    Zs[e] = Zx[i * RP + k];
+    Zs[r * r + e] = Zy[i * RP + k];
+  }
+}
+
+// max |E| over n entries, NaN-propagating; every thread gets the result.
+// `red`: 8 entries of shared scratch.  Contains two block barriers.
+template <typename W>
+__device__ W block_max_abs(const W* E, int n, W* red) {
+  auto take = [](W a, W b) { return (b > a || b != b) ? b : a; };
+  W mx = W(0);
+  for (int e = threadIdx.x; e < n; e += AD_NT) mx = take(mx, fabs(E[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = take(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < AD_NT / 32; ++w) mx = take(mx, red[w]);
+  __syncthreads();
+  return mx;
+}
+
+// -Gm^-1 for the SPD Gm (r x RP, zero padding).  The matrices of Alg. 4's
+// two solves move little from one sweep to the next, so the previous
+// sweep's Z = -Gm_prev^-1 is refined by Newton-Schulz steps: with
+// E = I + Gm Z, Z (I + E) = Z + Z E has residual E^2.  One step when
+// |E| <= tol1, two when |E| <= tol2 (the residual then is below the
+// working precision); otherwise, and on the first sweep, the sweep
+// operator.  Returns the buffer holding the result (Z, F or Gm).  The
+// choice depends only on the data, so every CTA makes the same one.
+template <typename W, int RMAX>
+__device__ W* refine_or_invert(W* Gm, W* Z, W* E, W* F, W* vbuf, int r,
+                               int RP, bool have, int32_t* status) {
+  const W tol1 = sizeof(W) == 8 ? W(1e-8) : W(3e-4);
+  const W tol2 = sizeof(W) == 8 ? W(1e-4) : W(2e-2);
+  if (have) {
+    // E = I + Gm Z
+    quad_mm<W>(E, RP, Gm, RP, 1, Z, r, r, W(1), nullptr, 0, r, W(1), 0, false);
+    __syncthreads();
+    const W e = block_max_abs<W>(E, r * RP, vbuf);
+    if (e <= tol2) {
+      // F = Z + Z E
+      quad_mm<W>(F, RP, Z, RP, 1, E, r, r, W(1), Z, RP, r, W(0), 0, true);
+      __syncthreads();
+      if (e <= tol1) return F;
+      // E = I + Gm F;  Z = F + F E
+      quad_mm<W>(E, RP, Gm, RP, 1, F, r, r, W(1), nullptr, 0, r, W(1), 0,
+                 false);
+      __syncthreads();
+      quad_mm<W>(Z, RP, F, RP, 1, E, r, r, W(1), F, RP, r, W(0), 0, true);
+      __syncthreads();
+      return Z;
+    }
+  }
+  fast_sweep_inverse<W, RMAX>(Gm, vbuf, r, RP, status);
+  return Gm;
+}
+
 // SX, SY^T: the reduced shares (global memory written by other CTAs, read
 // through L2, or this CTA's shared memory when sxy_smem).
+// have: Zx, Zy hold the previous sweep's inverses.
 template <typename W, int RMAX>
 __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
-                           uint64_t* sub = nullptr, const W* SXp = nullptr,
-                           const W* SYp = nullptr, bool sxy_smem = false) {
+                           bool have, uint64_t* sub = nullptr,
+                           const W* SXp = nullptr, const W* SYp = nullptr,
+                           bool sxy_smem = false) {
   if (!SXp) { SXp = a.SX; SYp = a.SY; }
   const int r = a.r, d = a.d, RP = o.RP, Q = RP / 4;
   uint64_t tm = sub ? globaltimer_ns() : 0;
@@ -183,10 +263,15 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
              d * Q, false);
   __syncthreads();
   mark(0);
-  fast_sweep_inverse<W, RMAX>(G, sm + o.v, r, RP, a.status);
+  W* Zx = sm + o.Zx;
+  W* Zy = sm + o.Zy;
+  const W* Ix = refine_or_invert<W, RMAX>(G, Zx, sm + o.E, sm + o.F, sm + o.v,
+                                          r, RP, have, a.status);
   mark(1);
-  // Xt = M (Yt Yt^T + lam I)^-1 = -M G
-  quad_mm<W>(Xt, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
+  // Xt = M (Yt Yt^T + lam I)^-1 = -M Ix;  Ix kept in Zx
+  quad_mm<W>(Xt, RP, M, RP, 1, Ix, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
+  if (Ix != Zx)
+    for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zx[e] = Ix[e];
   __syncthreads();
   mark(2);
   // M = SY^T + At^T Xt (d x RP);  G = Xt^T Xt + phi I
@@ -195,10 +280,13 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
              d * Q, false);
   __syncthreads();
   mark(3);
-  fast_sweep_inverse<W, RMAX>(G, sm + o.v, r, RP, a.status);
+  const W* Iy = refine_or_invert<W, RMAX>(G, Zy, sm + o.E, sm + o.F, sm + o.v,
+                                          r, RP, have, a.status);
   mark(4);
-  // Yt^T = M (Xt^T Xt + phi I)^-1 = -M G
-  quad_mm<W>(YtT, RP, M, RP, 1, G, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
+  // Yt^T = M (Xt^T Xt + phi I)^-1 = -M Iy;  Iy kept in Zy
+  quad_mm<W>(YtT, RP, M, RP, 1, Iy, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
+  if (Iy != Zy)
+    for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zy[e] = Iy[e];
   __syncthreads();
   mark(5);
   for (int e = threadIdx.x; e < d * r; e += AD_NT) {
@@ -397,10 +485,13 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
     const int k = e / r, bb = e % r;
     sm[o.YtT + k * RP + bb] = __ldcg(a.Yt + bb * d + k);
   }
+  // a resumed run continues from the inverses the last launch kept
+  const bool have0 = a.resume && __ldcg(a.kcount) > 0;
+  if (have0) load_inverses<W>(a.Zs, r, RP, sm + o.Zx, sm + o.Zy);
   __syncthreads();
   for (int it = 0; it < a.iters; ++it) {
     uint64_t t0 = prof ? globaltimer_ns() : 0;
-    small_fast<W, RMAX>(a, sm, o, prof ? tsub : nullptr);
+    small_fast<W, RMAX>(a, sm, o, have0 || it > 0, prof ? tsub : nullptr);
     uint64_t t1 = prof ? globaltimer_ns() : 0;
     sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 7 : nullptr,
                              gridDim.x, blockIdx.x,
@@ -424,6 +515,7 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
       a.Yt[bb * d + k] = sm[o.YtT + k * RP + bb];
       if (a.iters > 0) a.Xt[e] = sm[o.Xt + k * RP + bb];
     }
+    if (a.iters > 0) store_inverses<W>(a.Zs, r, RP, sm + o.Zx, sm + o.Zy);
     if (threadIdx.x == 0) *a.kcount += a.iters;
   }
   if (prof) {

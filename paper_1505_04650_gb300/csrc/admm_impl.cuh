@@ -51,6 +51,7 @@ struct AdmmArgs {
   W* Yt;      // state r x d
   W* Xt;      // state d x r
   int64_t* kcount;
+  W* Zs;      // state: kept inverses, 2 x r x r
   W* SX;      // d x r (reduced)
   W* SY;      // r x d (reduced)
   W* part;    // G x (2 d r + r d)
@@ -375,9 +376,15 @@ __global__ void __launch_bounds__(AD_NT) k_admm(AdmmArgs<W> a) {
 #include "admm_fast.cuh"
 #include "admm_batch.cuh"
 
+// State: Lam, Phit, Yt, Xt (W), then int64 k at the next 8-byte boundary
+// (state_core), then the two kept r x r inverses (W).
+inline size_t state_core(int64_t m, int64_t n, int r, int d, size_t e) {
+  const size_t b = ((size_t)m * r + (size_t)n * r + 2 * (size_t)r * d) * e;
+  return (b + 7) & ~size_t(7);
+}
 inline size_t state_bytes(int64_t m, int64_t n, int r, int d, size_t e) {
-  size_t b = ((size_t)m * r + (size_t)n * r + 2 * (size_t)r * d) * e;
-  return ((b + 7) & ~size_t(7)) + 8;
+  return state_core(m, n, r, d, e) + 8 +
+         ((2 * (size_t)r * r * e + 7) & ~size_t(7));
 }
 
 inline size_t factor_ws(int r, int d, size_t e, int G) {
@@ -480,7 +487,8 @@ static cnmf_status run_factor(const void* L, const void* Rt, const void* At,
   a.Phit = a.Lam + (size_t)m * r;
   a.Yt = a.Phit + (size_t)n * r;
   a.Xt = a.Yt + (size_t)r * d;
-  a.kcount = (int64_t*)(st + state_bytes(m, n, r, d, e) - 8);
+  a.kcount = (int64_t*)(st + state_core(m, n, r, d, e));
+  a.Zs = (W*)(st + state_core(m, n, r, d, e) + 8);
   a.L = (const W*)L; a.Rt = (const W*)Rt; a.At = (const W*)At;
   a.U = (W*)U; a.Vt = (W*)Vt;
   a.status = status;

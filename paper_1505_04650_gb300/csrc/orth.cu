@@ -55,8 +55,13 @@ template <int KP, bool SYM>
 struct GramMap {
   static constexpr int NB = KP / 4;
   static constexpr int NSUB = SYM ? NB * (NB + 1) / 2 : NB * NB;
+  // With fewer 4x4 sub-blocks than threads, RPH threads share a sub-block
+  // and take every RPH-th staged row; their sums are added in phase order.
+  static constexpr int RPH = NSUB >= OR_NT ? 1 : OR_NT / NSUB;
   static constexpr int SPT = (NSUB + OR_NT - 1) / OR_NT;
   static constexpr int PITCH = KP + 4;  // staged rows: 16B aligned, skewed
+  // shared scratch (doubles) that store() needs for the phase sums
+  static constexpr int RED = RPH > 1 ? RPH * NSUB * 16 : 0;
   __device__ static void block_of(int sb, int& ba, int& bb) {
     if (SYM) {
       int r = 0, rem = sb;
@@ -73,11 +78,15 @@ struct GramState {
   typedef GramMap<KP, SYM> M;
   GAcc<W> acc[M::SPT][16];
   int ba[M::SPT], bb[M::SPT];
+  int ph;
   __device__ __forceinline__ void init() {
+    ph = M::RPH > 1 ? (int)threadIdx.x / M::NSUB : 0;
 #pragma unroll
     for (int j = 0; j < M::SPT; ++j) {
-      int sb = threadIdx.x + j * OR_NT;
-      if (sb < M::NSUB) M::block_of(sb, ba[j], bb[j]); else { ba[j] = -1; bb[j] = -1; }
+      const int sb = M::RPH > 1 ? (int)threadIdx.x % M::NSUB
+                                : (int)threadIdx.x + j * OR_NT;
+      if (sb < M::NSUB && ph < M::RPH) M::block_of(sb, ba[j], bb[j]);
+      else { ba[j] = -1; bb[j] = -1; }
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[j][e].zero();
     }
@@ -87,7 +96,7 @@ struct GramState {
 #pragma unroll
     for (int j = 0; j < M::SPT; ++j) {
       if (ba[j] < 0) continue;
-      for (int r = 0; r < nrows; ++r) {
+      for (int r = ph; r < nrows; r += M::RPH) {
         W x[4], y[4];
         ldsN<4, W>(Xs + r * M::PITCH + 4 * ba[j], x);
         ldsN<4, W>(Ys + r * M::PITCH + 4 * bb[j], y);
@@ -98,15 +107,35 @@ struct GramState {
       }
     }
   }
-  __device__ __forceinline__ void store(double* out) const {
+  // Called by every thread of the block.  `red`: M::RED doubles of shared
+  // memory (unused when M::RPH == 1).
+  __device__ __forceinline__ void store(double* out, double* red) const {
+    if (M::RPH == 1) {
 #pragma unroll
-    for (int j = 0; j < M::SPT; ++j) {
-      if (ba[j] < 0) continue;
+      for (int j = 0; j < M::SPT; ++j) {
+        if (ba[j] < 0) continue;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-          out[(4 * ba[j] + a) * KP + 4 * bb[j] + b] = acc[j][a * 4 + b].value();
+          for (int b = 0; b < 4; ++b)
+            out[(4 * ba[j] + a) * KP + 4 * bb[j] + b] = acc[j][a * 4 + b].value();
+      }
+      return;
+    }
+    const int sb = (int)threadIdx.x % M::NSUB;
+    __syncthreads();   // the caller's staging buffers may alias `red`
+    if (ba[0] >= 0)
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        red[(ph * M::NSUB + sb) * 16 + e] = acc[0][e].value();
+    __syncthreads();
+    if (ba[0] >= 0 && ph == 0) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        double t = 0.0;
+        for (int q = 0; q < M::RPH; ++q) t += red[(q * M::NSUB + sb) * 16 + e];
+        out[(4 * ba[0] + e / 4) * KP + 4 * bb[0] + e % 4] = t;
+      }
     }
   }
 };
@@ -117,16 +146,31 @@ struct PanelDesc {
   int64_t ldx, ldy, rows;
 };
 
+// One tile of OR_ROWS panel rows held in registers on its way to shared
+// memory: all loads are issued before the first use, and the next tile is
+// loaded while the current one is being consumed.
 template <typename W, int KP>
-__device__ __forceinline__ void stage_rows(W* dst, const W* __restrict__ src,
-                                           int64_t ld, int64_t r0, int nrows,
-                                           int k) {
-  constexpr int PITCH = KP + 4;
-  for (int e = threadIdx.x; e < OR_ROWS * KP; e += OR_NT) {
-    int r = e / KP, c = e % KP;
-    dst[r * PITCH + c] = (r < nrows && c < k) ? src[(r0 + r) * ld + c] : W(0);
+struct RowTile {
+  static constexpr int NIT = OR_ROWS * KP / OR_NT;
+  W v[NIT];
+  __device__ __forceinline__ void load(const W* __restrict__ src, int64_t ld,
+                                       int64_t r0, int nrows, int k) {
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int e = threadIdx.x + it * OR_NT;
+      const int r = e / KP, c = e % KP;
+      v[it] = (r < nrows && c < k) ? src[(r0 + r) * ld + c] : W(0);
+    }
   }
-}
+  __device__ __forceinline__ void store(W* dst) const {
+    constexpr int PITCH = KP + 4;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int e = threadIdx.x + it * OR_NT;
+      dst[(e / KP) * PITCH + e % KP] = v[it];
+    }
+  }
+};
 
 // Gram (SYM) or cross products over row ranges; per-CTA partials, FP64.
 template <typename W, int KP, bool SYM>
@@ -141,16 +185,112 @@ __global__ void __launch_bounds__(OR_NT)
   const int64_t r0 = (c * P.rows) / G, r1 = ((c + 1) * P.rows) / G;
   GramState<W, KP, SYM> gs;
   gs.init();
+  RowTile<W, KP> tx, ty;
+  if (r0 < r1) {
+    const int nr = (int)std::min<int64_t>(OR_ROWS, r1 - r0);
+    tx.load((const W*)P.X, P.ldx, r0, nr, k);
+    if (!SYM) ty.load((const W*)P.Y, P.ldy, r0, nr, k);
+  }
   for (int64_t rb = r0; rb < r1; rb += OR_ROWS) {
-    int nr = (int)std::min<int64_t>(OR_ROWS, r1 - rb);
-    stage_rows<W, KP>(Xs, (const W*)P.X, P.ldx, rb, nr, k);
-    if (!SYM) stage_rows<W, KP>(Ys, (const W*)P.Y, P.ldy, rb, nr, k);
+    const int nr = (int)std::min<int64_t>(OR_ROWS, r1 - rb);
+    tx.store(Xs);
+    if (!SYM) ty.store(Ys);
     __syncthreads();
+    const int64_t rn = rb + OR_ROWS;
+    if (rn < r1) {   // next tile in flight during the accumulation
+      const int nn = (int)std::min<int64_t>(OR_ROWS, r1 - rn);
+      tx.load((const W*)P.X, P.ldx, rn, nn, k);
+      if (!SYM) ty.load((const W*)P.Y, P.ldy, rn, nn, k);
+    }
     gs.accumulate(Xs, SYM ? Xs : Ys, nr);
     __syncthreads();
   }
-  gs.store(part + ((size_t)blockIdx.y * G + c) * KP * KP);
+  gs.store(part + ((size_t)blockIdx.y * G + c) * KP * KP,
+           reinterpret_cast<double*>(smem));
 }
+
+// Double-float numbers for the small factorisations of FP32 panels: value
+// = hi + lo with |lo| <= ulp(hi) / 2, on the FP32 pipe (GB300's FP64 pipe
+// is a small fraction of it).  Built from error-free transformations --
+// Knuth's TwoSum, Dekker's FastTwoSum, the FMA product split -- and one
+// Newton correction for the square root and the reciprocal (Karp and
+// Markstein's scheme); about 2^-44 relative per operation.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_fast(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  DF s = df_two_sum(x.hi, y.hi);
+  const DF t = df_two_sum(x.lo, y.lo);
+  s.lo += t.hi;
+  s = df_fast(s.hi, s.lo);
+  s.lo += t.lo;
+  return df_fast(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_fast(p, e);
+}
+__device__ __forceinline__ DF df_sqrt(DF x) {   // x > 0
+  const float r = sqrtf(x.hi);
+  const float p = r * r, pe = fmaf(r, r, -p);
+  const float res = ((x.hi - p) - pe) + x.lo;   // x - r^2
+  return df_fast(r, res / (2.0f * r));
+}
+__device__ __forceinline__ DF df_rcp(DF y) {
+  const float q = 1.0f / y.hi;
+  const DF qy = df_mul(DF{q, 0.0f}, y);
+  const DF res = df_add(DF{1.0f, 0.0f}, DF{-qy.hi, -qy.lo});   // 1 - q y
+  return df_fast(q, res.hi / y.hi);
+}
+
+// Arithmetic of the Cholesky factorisation: FP64 for FP64 panels,
+// double-float for FP32 ones.  Both elements are 8 bytes.
+struct ArF64 {
+  typedef double T;
+  static __device__ __forceinline__ T from(double d) { return d; }
+  static __device__ __forceinline__ double lead(T x) { return x; }
+  static __device__ __forceinline__ T one() { return 1.0; }
+  static __device__ __forceinline__ T root(T x) { return sqrt(x); }
+  static __device__ __forceinline__ T rcp(T x) { return 1.0 / x; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  // c - a b s
+  static __device__ __forceinline__ T update(T c, T a, T b, T s) {
+    return fma(-s, a * b, c);
+  }
+};
+struct ArDF {
+  typedef DF T;
+  static __device__ __forceinline__ T from(double d) {
+    const float h = (float)d;
+    return DF{h, (float)(d - (double)h)};
+  }
+  static __device__ __forceinline__ double lead(T x) { return (double)x.hi; }
+  static __device__ __forceinline__ T one() { return DF{1.0f, 0.0f}; }
+  static __device__ __forceinline__ T root(T x) { return df_sqrt(x); }
+  static __device__ __forceinline__ T rcp(T x) { return df_rcp(x); }
+  static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+  static __device__ __forceinline__ T update(T c, T a, T b, T s) {
+    const DF t = df_mul(df_mul(a, b), s);
+    return df_add(c, DF{-t.hi, -t.lo});
+  }
+};
+template <typename W>
+struct ArOf;
+template <>
+struct ArOf<double> { typedef ArF64 type; };
+template <>
+struct ArOf<float> { typedef ArDF type; };
 
 // Sum partials (CTA order).  mode 0: write C (W, pitch ldc, k x k).
 // mode 1: the last CTA of each panel factors G + shift I = R^T R (FP64) and
@@ -202,65 +342,120 @@ __global__ void __launch_bounds__(OR_NT)
   if (!last_s) return;
   __threadfence();
 
+  typedef typename ArOf<W>::type Ar;
+  typedef typename Ar::T T;
+  static_assert(sizeof(T) == 8, "8-byte factor entries");
   extern __shared__ __align__(16) unsigned char smem[];
-  double* R = reinterpret_cast<double*>(smem);                // KP x KP
+  T* R = reinterpret_cast<T*>(smem);                       // KP x KP
   __shared__ double trace_s;
   __shared__ int bad_s;
-  const volatile double* gv = gfull + (size_t)p * KP * KP;
+  // the other CTAs' sums: L2 reads (after the ticket's fence), all issued
+  // at once; the Gram's upper triangle is staged in the factor's slots
+  const double* gp = gfull + (size_t)p * KP * KP;
+  double* Gs = reinterpret_cast<double*>(R);   // same 8-byte slots
   for (int i = threadIdx.x; i < KP * KP; i += OR_NT) {
-    int ia = i / KP, ib = i % KP;
-    R[i] = (ia <= ib && ia < k && ib < k) ? gv[i] : 0.0;
+    const int ia = i / KP, ib = i % KP;
+    Gs[i] = (ia <= ib && ia < k && ib < k) ? __ldcg(gp + i) : 0.0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double tr = 0.0;
-    int bad = 0;
-    for (int j = 0; j < k; ++j) tr += R[j * KP + j];
-    if (!isfinite(tr)) bad = CNMF_E_NONFINITE;
+    for (int j = 0; j < k; ++j) tr += Gs[j * KP + j];
     trace_s = tr;
-    bad_s = bad;
+    bad_s = isfinite(tr) ? 0 : CNMF_E_NONFINITE;
+    if (bad_s) set_status(status, bad_s);
   }
   __syncthreads();
-  if (bad_s) {
-    if (threadIdx.x == 0) set_status(status, bad_s);
-  }
   const double shift = shift_rel * trace_s + shift_abs;
-  for (int j = threadIdx.x; j < k; j += OR_NT) R[j * KP + j] += shift;
+  for (int i = threadIdx.x; i < KP * KP; i += OR_NT) {
+    const int ia = i / KP, ib = i % KP;
+    const double g = Gs[i] + ((ia == ib && ia < k) ? shift : 0.0);
+    R[i] = Ar::from(g);
+  }
   __syncthreads();
-  // right-looking Cholesky, upper factor in place
-  for (int j = 0; j < k; ++j) {
-    if (threadIdx.x == 0) {
-      double d = R[j * KP + j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        set_status(status, isfinite(d) ? CNMF_E_CHOLESKY : CNMF_E_NONFINITE);
-        d = 1.0;
-      }
-      R[j * KP + j] = sqrt(d);
+  // Right-looking Cholesky, upper factor in place, one barrier per pivot.
+  // Thread 0 owns the pivots: in the phase of pivot j it also finishes the
+  // update of the diagonal entry j + 1 and forms its root and reciprocal,
+  // once.  The other threads update the trailing triangle with the
+  // unscaled row j times 1/R_jj^2 and scale row j - 1, which nobody reads
+  // in this phase.
+  __shared__ T piv_s[3][3];   // {root, 1/root, 1/root^2}, pivot j in j % 3
+  auto pivot = [&](int j) {
+    T d = R[j * KP + j];
+    const double dl = Ar::lead(d);
+    if (!(dl > 0.0) || !isfinite(dl)) {
+      set_status(status, isfinite(dl) ? CNMF_E_CHOLESKY : CNMF_E_NONFINITE);
+      d = Ar::one();
     }
-    __syncthreads();
-    const double dj = R[j * KP + j];
-    for (int l = j + 1 + threadIdx.x; l < k; l += OR_NT) R[j * KP + l] /= dj;
-    __syncthreads();
+    const T rt = Ar::root(d);
+    const T iv = Ar::rcp(rt);
+    piv_s[j % 3][0] = rt;
+    piv_s[j % 3][1] = iv;
+    piv_s[j % 3][2] = Ar::mul(iv, iv);
+  };
+  if (threadIdx.x == 0 && k > 0) pivot(0);
+  __syncthreads();
+  // phase j reads slots (j - 1) % 3 and j % 3 and writes (j + 1) % 3
+  for (int j = 0; j <= k; ++j) {
+    if (j > 0) {   // scale row j - 1
+      const int jp = j - 1;
+      const T iv = piv_s[jp % 3][1];
+      for (int l = jp + 1 + threadIdx.x; l < k; l += OR_NT)
+        R[jp * KP + l] = Ar::mul(R[jp * KP + l], iv);
+      if (threadIdx.x == 0) R[jp * KP + jp] = piv_s[jp % 3][0];
+    }
+    if (j == k) break;
+    const T iv2 = piv_s[j % 3][2];
     const int nt = k - j - 1;
+    // entry (j+1, j+1) is t == 0: thread 0, which then forms pivot j + 1
     for (int t = threadIdx.x; t < nt * nt; t += OR_NT) {
-      int ia = j + 1 + t / nt, ib = j + 1 + t % nt;
-      if (ia <= ib) R[ia * KP + ib] -= R[j * KP + ia] * R[j * KP + ib];
+      const int ia = j + 1 + t / nt, ib = j + 1 + t % nt;
+      if (ia <= ib)
+        R[ia * KP + ib] =
+            Ar::update(R[ia * KP + ib], R[j * KP + ia], R[j * KP + ib], iv2);
     }
+    if (threadIdx.x == 0 && nt > 0) pivot(j + 1);
     __syncthreads();
   }
-  // R^-1 (upper) straight into `out`: thread jc owns column jc, rows
-  // bottom-up in lockstep (so R[i][l] reads are broadcasts).
-  for (int jc = threadIdx.x; jc < KP; jc += OR_NT) {
-    for (int i = KP - 1; i >= 0; --i) {
-      W v = W(0);
-      if (i <= jc && jc < k) {
-        W s = (i == jc) ? W(1) : W(0);
-        for (int l = i + 1; l <= jc; ++l) s -= (W)R[i * KP + l] * out[l * KP + jc];
-        v = s / (W)R[i * KP + i];
-      }
-      out[i * KP + jc] = v;
-    }
+  __syncthreads();
+  // R^-1 in the working precision, in place in `Ri` (upper, k x k), column
+  // by column: column j needs the inverted leading block and a copy of the
+  // old column j.  GI threads per row share each dot product and add their
+  // parts by shuffles in a fixed order; the copy of column j + 1 is taken in
+  // the same phase (double buffer); diagonal reciprocals are formed first,
+  // all at once.
+  constexpr int GI = OR_NT / KP >= 16 ? 16 : OR_NT / KP >= 8 ? 8
+                     : OR_NT / KP >= 4 ? 4 : 2;
+  static_assert(GI * KP <= OR_NT, "one row group per KP row");
+  // FP64 panels invert in place in R; FP32 ones in a copy after it
+  W* tail = reinterpret_cast<W*>(R + KP * KP);
+  W* Ri = sizeof(W) == 8 ? reinterpret_cast<W*>(R) : tail;   // KP x KP
+  W* colv = sizeof(W) == 8 ? tail : tail + KP * KP;          // 2 x KP
+  W* dinv = colv + 2 * KP;                                   // KP
+  for (int i = threadIdx.x; i < KP * KP; i += OR_NT) {
+    const int ia = i / KP, ib = i % KP;
+    Ri[i] = (ia <= ib && ib < k) ? (W)Ar::lead(R[i]) : W(0);
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += OR_NT) dinv[j] = W(1) / Ri[j * KP + j];
+  if (threadIdx.x == 0) colv[0] = Ri[0];
+  __syncthreads();
+  const int irow = threadIdx.x / GI, ig = threadIdx.x % GI;
+  for (int j = 0; j < k; ++j) {
+    const W* cj = colv + (j & 1) * KP;
+    W* cn = colv + ((j + 1) & 1) * KP;
+    W x = W(0);
+    if (irow < j)
+      for (int l = irow + ig; l < j; l += GI) x = fma(Ri[irow * KP + l], cj[l], x);
+#pragma unroll
+    for (int o = GI / 2; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o, GI);
+    if (j + 1 < k)
+      for (int l = threadIdx.x; l <= j + 1; l += OR_NT) cn[l] = Ri[l * KP + j + 1];
+    if (ig == 0 && irow < j) Ri[irow * KP + j] = -dinv[j] * x;
+    if (threadIdx.x == 0) Ri[j * KP + j] = dinv[j];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < KP * KP; i += OR_NT) out[i] = Ri[i];
   if (threadIdx.x == 0) tickets[p] = 0;
 }
 
@@ -288,10 +483,15 @@ __global__ void __launch_bounds__(OR_NT)
   GramState<W, KP, true> gs;
   if (GRAM) gs.init();
   const int r = threadIdx.x / 8, c0 = (threadIdx.x % 8) * TN;
+  RowTile<W, KP> ty;
+  if (r0 < r1) ty.load((const W*)P.Y, P.ldy, r0, (int)std::min<int64_t>(OR_ROWS, r1 - r0), k);
   for (int64_t rb = r0; rb < r1; rb += OR_ROWS) {
     int nr = (int)std::min<int64_t>(OR_ROWS, r1 - rb);
-    stage_rows<W, KP>(Ys, (const W*)P.Y, P.ldy, rb, nr, k);
+    ty.store(Ys);
     __syncthreads();
+    const int64_t rn = rb + OR_ROWS;
+    if (rn < r1)
+      ty.load((const W*)P.Y, P.ldy, rn, (int)std::min<int64_t>(OR_ROWS, r1 - rn), k);
     W q[TN];
 #pragma unroll
     for (int t = 0; t < TN; ++t) q[t] = W(0);
@@ -312,7 +512,8 @@ __global__ void __launch_bounds__(OR_NT)
     if (GRAM) gs.accumulate(Qs, Qs, nr);
     __syncthreads();
   }
-  if (GRAM) gs.store(part + ((size_t)p * G + c) * KP * KP);
+  if (GRAM) gs.store(part + ((size_t)p * G + c) * KP * KP,
+                     reinterpret_cast<double*>(smem));
 }
 
 static int orth_kp(int k) { return pad_k(k); }
@@ -339,15 +540,30 @@ size_t cross_workspace(int64_t rows, int k, cnmf_dtype w) {
 }
 
 template <typename W, int KP>
+static size_t finish_smem() {
+  return sizeof(double) * KP * KP +
+         sizeof(W) * ((sizeof(W) == 8 ? 0 : KP * KP) + 3 * KP);
+}
+template <typename W, int KP, bool SYM>
+static size_t gram_smem() {
+  const size_t stage = sizeof(W) * (SYM ? 1 : 2) * OR_ROWS * (KP + 4);
+  return std::max(stage, sizeof(double) * GramMap<KP, SYM>::RED);
+}
+template <typename W, int KP>
+static size_t apply_smem() {
+  const size_t stage = sizeof(W) * (KP * KP + 2 * OR_ROWS * (KP + 4));
+  return std::max(stage, sizeof(double) * GramMap<KP, true>::RED);
+}
+
+template <typename W, int KP>
 static void set_smem_attrs() {
   static std::once_flag once;
   std::call_once(once, [] {
-    size_t fin = sizeof(double) * KP * KP;
+    size_t fin = finish_smem<W, KP>();
     set_max_smem((const void*)k_finish<W, KP>, fin);
-    size_t ap = sizeof(W) * (KP * KP + 2 * OR_ROWS * (KP + 4));
-    size_t gx = sizeof(W) * 2 * OR_ROWS * (KP + 4);
-    set_max_smem((const void*)k_gram<W, KP, false>, gx);
-    set_max_smem((const void*)k_gram<W, KP, true>, gx);
+    size_t ap = apply_smem<W, KP>();
+    set_max_smem((const void*)k_gram<W, KP, false>, gram_smem<W, KP, false>());
+    set_max_smem((const void*)k_gram<W, KP, true>, gram_smem<W, KP, true>());
     set_max_smem((const void*)k_apply<W, KP, true>, ap);
     set_max_smem((const void*)k_apply<W, KP, false>, ap);
   });
@@ -373,11 +589,11 @@ static cnmf_status run_orth(const OrthPanel* pp, int np, int k, void* ws,
   }
   dim3 grid(G, np);
   const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
-  const size_t fin_smem = sizeof(double) * KP * KP;
-  const size_t ap_smem = sizeof(W) * (KP * KP + 2 * OR_ROWS * (KP + 4));
+  const size_t fin_smem = finish_smem<W, KP>();
+  const size_t ap_smem = apply_smem<W, KP>();
   const double shift = sizeof(W) == 8 ? 1e-13 : 1e-11;
 
-  k_gram<W, KP, true><<<grid, OR_NT, sizeof(W) * OR_ROWS * (KP + 4), s>>>(
+  k_gram<W, KP, true><<<grid, OR_NT, gram_smem<W, KP, true>(), s>>>(
       d[0], d[1], k, part);
   CNMF_CHECK_LAUNCH();
   k_finish<W, KP><<<dim3(nfin, np), OR_NT, fin_smem, s>>>(
@@ -408,7 +624,7 @@ static cnmf_status run_cross(const void* X, int64_t ldx, const void* Y,
   double* part = cv.take<double>((size_t)2 * G * KP * KP);
   PanelDesc d{X, Y, ldx, ldy, rows};
   k_gram<W, KP, false><<<dim3(G, 1), OR_NT,
-                         sizeof(W) * 2 * OR_ROWS * (KP + 4), s>>>(d, d, k,
+                         gram_smem<W, KP, false>(), s>>>(d, d, k,
                                                                   part);
   CNMF_CHECK_LAUNCH();
   const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
@@ -431,11 +647,11 @@ static cnmf_status run_gram_chol(const void* Y, int64_t ld, int64_t rows,
   unsigned* tickets = cv.take<unsigned>(64);
   CNMF_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s));
   PanelDesc d{Y, Y, ld, ld, rows};
-  k_gram<W, KP, true><<<dim3(G, 1), OR_NT, sizeof(W) * OR_ROWS * (KP + 4), s>>>(
+  k_gram<W, KP, true><<<dim3(G, 1), OR_NT, gram_smem<W, KP, true>(), s>>>(
       d, d, k, part);
   CNMF_CHECK_LAUNCH();
   const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
-  const size_t fin_smem = sizeof(double) * KP * KP;
+  const size_t fin_smem = finish_smem<W, KP>();
   k_finish<W, KP><<<dim3(nfin, 1), OR_NT, fin_smem, s>>>(
       part, G, k, 1, 0.0, shift_abs, gfull, (W*)rinv_out, (W*)rinv_out, 0,
       tickets, status);

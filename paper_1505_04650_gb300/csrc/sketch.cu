@@ -235,7 +235,10 @@ __global__ void k_prod_fixup(W* __restrict__ Z, int64_t ldz, int kz, int64_t P,
   if (threadIdx.x == 0) nc_s = nc;
   __syncthreads();
   const int64_t p0 = tp * SK_BP;
-  for (int e = threadIdx.x; e < SK_BP * KP; e += blockDim.x) {
+  // blockIdx.y splits the tile's entries: one or a few per thread, so the
+  // partial loads of all entries are in flight together
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < SK_BP * KP;
+       e += blockDim.x * gridDim.y) {
     int lp = e / KP, col = e % KP;
     if (p0 + lp >= P || col >= kz) continue;
     W s = W(0);
@@ -287,7 +290,7 @@ static cnmf_status run_prod(const ProdArgs& a, void* ws, cudaStream_t s) {
       b_vec, (W*)a.Z, a.ldz, a.kz, part, U, chunks);
   CNMF_CHECK_LAUNCH();
   if (chunks > 1) {
-    k_prod_fixup<W, KP><<<(unsigned)tiles, 256, 0, s>>>(
+    k_prod_fixup<W, KP><<<dim3((unsigned)tiles, KP / 2), 256, 0, s>>>(
         (W*)a.Z, a.ldz, a.kz, P, part, U, chunks, G);
     CNMF_CHECK_LAUNCH();
   }
@@ -329,7 +332,8 @@ cnmf_status launch_prod_fixup_f32(void* Z, int64_t ldz, int kz, int64_t P,
   const unsigned tiles = (unsigned)ceil_div(P, SK_BP);
 #define FIX_CASE(K)                                                      \
   case K:                                                                \
-    k_prod_fixup<float, K><<<tiles, 256, 0, s>>>((float*)Z, ldz, kz, P,   \
+    k_prod_fixup<float, K><<<dim3(tiles, K / 2), 256, 0, s>>>(            \
+        (float*)Z, ldz, kz, P,                                           \
                                                  part, U, chunks, G);    \
     break;
   switch (KP) {

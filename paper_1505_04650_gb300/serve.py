@@ -57,6 +57,7 @@ class Request:
     cluster_size: int = 1
     rho: float = math.nan
     floor: float = math.nan
+    floor_uv: tuple | None = None
     nbytes: int = 0
     done_sweeps: int = 0
     problem: BatchProblem | None = None
@@ -84,6 +85,21 @@ def make_workload(nreq: int, rate: float, seed: int = 0, m_range=(200, 4000),
         reqs.append(Request(i, float(t[i]), m, n, r, r + 10, q, iters, sigma,
                             seed=10_000 * (seed + 1) + i))
     return reqs
+
+
+def truncation_factors(L: torch.Tensor, Rt: torch.Tensor, Atilde: torch.Tensor,
+                       r: int):
+    """(F, G) with F G^T = L Atilde_r R, Atilde_r the rank-r SVD truncation
+    of the compressed matrix: m x r and n x r FP32 factors.  The residual
+    ||A - F G^T|| is the best rank-r fit the sketch can express -- computed
+    as a residual, not as ||A||^2 - sum sigma_i^2, which cancels
+    catastrophically when the floor is small."""
+    U, s, Vh = torch.linalg.svd(Atilde.double().cpu())
+    Us = (U[:, :r] * s[:r]).to(L.device)
+    V = Vh[:r].T.contiguous().to(L.device)
+    F = (L.double() @ Us).float()
+    G = (Rt.double() @ V).float()
+    return F, G
 
 
 def request_bytes(rq: Request) -> int:
@@ -199,22 +215,24 @@ class Server:
         At = pb.Atilde
         lam = float(torch.linalg.norm(At.double())) / rq.r
         pb.lam = pb.phi = lam
-        s = torch.linalg.svdvals(At.double().cpu())
-        rq.floor_num = float((s[: rq.r] ** 2).sum())
+        # rank-r truncation of the compressed matrix, lifted back: the
+        # reference point for the request's residual target
+        rq.floor_uv = truncation_factors(pb.L, pb.Rt, At, rq.r)
         for t in (pb.L, pb.Rt, pb.Atilde, pb.U, pb.Vt, pb.state.buf,
                   pb.scratch, rq.A):
             t.record_stream(self.main)
         rq.t_compressed = now
 
-    def _finish(self, rq: Request, res: torch.Tensor):
+    def _finish(self, rq: Request, res: torch.Tensor, res_floor: torch.Tensor):
         e2, a2 = float(res[0]), float(res[1])
         rq.rho = math.sqrt(e2 / a2)
-        rq.floor = math.sqrt(max(0.0, 1.0 - rq.floor_num / a2))
+        rq.floor = math.sqrt(float(res_floor[0]) / a2)
         if rq.keep:
             rq.U = rq.problem.U.clone()
             rq.Vt = rq.problem.Vt.clone()
         rq.problem = None
         rq.A = None
+        rq.floor_uv = None
 
     def run(self, requests: list[Request], realtime: bool = True) -> dict:
         pending = collections.deque(sorted(requests, key=lambda q: q.t_arrive))
@@ -267,13 +285,13 @@ class Server:
                 running = [rq for rq in running if rq.done_sweeps < rq.iters]
                 outs = []
                 for rq in finished:
-                    outs.append(cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt))
+                    outs.append((cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt),
+                                 cnmf_residual(rq.A, *rq.floor_uv)))
                 self.main.synchronize()   # this round only; compressions go on
                 now = clock()
-                for rq, res in zip(finished, outs):
+                for rq, (res, resf) in zip(finished, outs):
                     rq.t_done = now
-                    res_h = res.cpu()
-                    self._finish(rq, res_h)
+                    self._finish(rq, res.cpu(), resf.cpu())
                     in_use -= rq.nbytes
                     done.append(rq)
             elif compressing:

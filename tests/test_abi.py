@@ -87,7 +87,8 @@ def test_workspace_queries(lib):
     assert lib.cnmf_compress_workspace(100, 80, 10, 1) > 0
     assert lib.cnmf_compress_workspace(100, 80, 200, 1) == 0
     assert lib.cnmf_factor_state_bytes(100, 80, 5, 10, 1) == \
-        ((100 * 5 + 80 * 5 + 2 * 5 * 10) * 4 + 7) // 8 * 8 + 8
+        ((100 * 5 + 80 * 5 + 2 * 5 * 10) * 4 + 7) // 8 * 8 + 8 + \
+        (2 * 5 * 5 * 4 + 7) // 8 * 8
     assert lib.snmf_select_workspace(100, 80, 10, 2) > 0
     assert lib.cnmf_plain_state_bytes(100, 80, 5, 0) == \
         (2 * 100 * 5 + 2 * 80 * 5) * 8 + 8

@@ -117,7 +117,9 @@ def _planted(rows, k, kappa, seed):
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("rows,k,kappa", [(50, 1, 1.0), (97, 7, 10.0),
                                           (3000, 30, 1e3), (20000, 30, 1e4),
-                                          (1000, 80, 1e2), (700, 128, 10.0)])
+                                          (1000, 80, 1e2), (700, 128, 10.0),
+                                          (400, 45, 1e2), (2000, 60, 1e3),
+                                          (500, 90, 10.0)])
 def test_orth_unique_q(storage, rows, k, kappa):
     torch = need_gpu()
     import paper_1505_04650_gb300 as cn

@@ -115,6 +115,45 @@ def _factor_case(m, n, r, d, q, sigma, seed, storage):
     return A, L, Rt, At, U0, V0
 
 
+def _check_kept_inverse(state, phi, storage):
+    """The state's kept Zy is -(Xt^T Xt + phi I)^-1 of the final Xt (the
+    inverse the last Y update used), whichever way the kernel formed it."""
+    sec = state._sections()
+    Xt = to_np(sec["Xt"])
+    Zy = to_np(sec["Z"][1])
+    r = Xt.shape[1]
+    ref = -np.linalg.inv(Xt.T @ Xt + phi * np.eye(r))
+    tol = 1e-10 if storage == "f64" else 1e-4
+    assert rel(Zy, ref) <= tol
+
+
+@pytest.mark.parametrize("storage,iters", [("f64", 300), ("f32", 300)])
+def test_factor_long_run_matches_oracle(storage, iters):
+    """Hundreds of sweeps: after the first few the solves' inverses are
+    refined from the previous sweep's, so this exercises that path."""
+    torch = need_gpu()
+    import paper_1505_04650_gb300 as cn
+    A, L, Rt, At, U0, V0 = _factor_case(500, 400, 10, 20, 4, 0.01, 1000,
+                                        storage)
+    lam = np.linalg.norm(At) / 10
+    w = wdt(storage)
+    dev = lambda x: torch.tensor(x, dtype=w).cuda()
+    Ud, Vtd = dev(U0), dev(V0.T.copy())
+    Ud, Vtd, state, st = cn.cnmf_factor(dev(L), dev(Rt), dev(At), Ud, Vtd,
+                                        lam, lam, iters)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = oadmm.admm(L, Rt, At, U0, V0, lam=lam, phi=lam, iters=iters)
+    eu, ev = rel(to_np(Ud), ref.U), rel(to_np(Vtd).T, ref.V)
+    print(f"{iters} sweeps: U rel err {eu:.2e}  V rel err {ev:.2e}")
+    tol = 1e-9 if storage == "f64" else 1e-3
+    assert eu <= tol and ev <= tol
+    _check_kept_inverse(state, lam, storage)
+    rg = ores.rel_residual(A, to_np(Ud), to_np(Vtd).T)
+    ro = ores.rel_residual(A, ref.U, ref.V)
+    assert abs(rg - ro) <= 1e-3 * ro
+
+
 @pytest.mark.parametrize("storage,m,n,r,d", [("f64", 500, 400, 10, 20),
                                              ("f32", 500, 400, 10, 20),
                                              ("f32", 3000, 2000, 20, 30),
@@ -137,6 +176,7 @@ def test_factor_20_sweeps_matches_oracle(storage, m, n, r, d):
     print(f"U rel err {eu:.2e}  V rel err {ev:.2e}")
     assert eu <= tol and ev <= tol
     assert int(state.k.item()) == 20
+    _check_kept_inverse(state, lam, storage)
     # final objective within 1e-3
     rg = ores.rel_residual(A, to_np(Ud), to_np(Vtd).T)
     ro = ores.rel_residual(A, ref.U, ref.V)
