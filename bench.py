@@ -73,6 +73,7 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)   # sampling is running when the timed region starts
         except OSError:
             self.proc = None
         return self
@@ -162,17 +163,51 @@ def run_reference(args):
 
 
 def launches_per_step(q, chunks_gt1=True):
-    """Library kernel launches of one step (compress + one factor launch)."""
-    prod = 2 if chunks_gt1 else 1
+    """Library kernel launches of one step (compress + one factor launch),
+    for FP32 A on the tensor-core product path: each product is a B-panel
+    pack, the product kernel and (split tiles) the fix-up."""
+    prod = 3 if chunks_gt1 else 2
     per_pass = 2 * prod + 5          # A., A^T., CholeskyQR2 of both panels
     compress = 2 + (2 * q + 1) * per_pass + prod + 2
     return compress + 1
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of the kernel as it stands, with the SHA-256 of the
+# sources it was compiled from; None once those sources change.
+TRAFFIC = {
+    # profiles/k_admm_fast_m20000_n10000_r20_d30.md: 8.538 MB read +
+    # 0.072 MB written by the 500-sweep launch
+    "k_admm_fast": {"bytes_per_unit": 8.610048e6 / 500, "sha": "c2bed439950a74ba"},
+    # profiles/k_tc_prod_f32_m20000_n10000_d30.md: A X 805.26 + 5.45 MB,
+    # A^T Y 868.12 + 4.17 MB; one unit = one pass (both products)
+    "k_tc_prod": {"bytes_per_unit": 1683.0e6, "sha": "598124c8a461d962"},
+}
+
+
+def _src_sha(kernel):
+    import hashlib
+    files = {"k_admm_fast": ["admm_fast.cuh", "admm_impl.cuh", "common.cuh"],
+             "k_tc_prod": ["tc.cu", "common.cuh"]}[kernel]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1505_04650_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, units):
+    t = TRAFFIC.get(kernel)
+    if not t or t["sha"] != _src_sha(kernel):
+        return None
+    return t["bytes_per_unit"] * units
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -282,7 +317,9 @@ def main(argv=None):
     breakdown["factor_phase_us_per_sweep"] = {
         k: float(v) / 1e3 / iters for k, v in zip(names, ph.cpu().tolist())}
 
-    # ---- dominant kernel: the products with A (one per side per pass)
+    # ---- the sketch products with A (one per side per pass), timed as a
+    # pass through the public call: B-panel packing + tensor-core product +
+    # split-tile fix-up, for A X and A^T Y
     X = torch.randn(n, d, device=dev)
     Y = torch.randn(m, d, device=dev)
     for _ in range(3):
@@ -295,14 +332,19 @@ def main(argv=None):
         cn.cnmf_sketch_pass(A, X, Y)
     e1.record(stream)
     torch.cuda.synchronize()
-    pass_ms = e0.elapsed_time(e1) / reps          # A X and A^T Y: two launches
-    flops_pass = 2 * 2.0 * m * n * d
+    pass_ms = e0.elapsed_time(e1) / reps          # A X and A^T Y
     bytes_pass = 2 * (4.0 * m * n + 4.0 * (m + n) * d)
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = _peaks()
-    ffma_peak = nsm * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
-    achieved_tf = flops_pass / (pass_ms * 1e-3) / 1e12
-    achieved_gbs = bytes_pass / (pass_ms * 1e-3) / 1e9
+    sketch_gbs = bytes_pass / (pass_ms * 1e-3) / 1e9
+
+    # ---- dominant kernel of the step: the compressed ADMM launch
+    # (k_admm_fast, all 500 sweeps in one cooperative launch), timed by the
+    # events around cnmf_factor above.  Algorithmic bytes per sweep: L, R^T
+    # (d each) and U, Lam, V^T, Phi^T (r each, read and written) per row:
+    # 4 (m + n)(d + 4 r).
+    admm_bytes = 4.0 * (m + n) * (d + 4 * r) * iters
+    admm_gbs = admm_bytes / (breakdown["factor_ms"] * 1e-3) / 1e9
+    traffic = _traffic("k_admm_fast", iters)
 
     out = {
         "metric": METRIC, "value": value, "unit": "factorizations/s",
@@ -313,19 +355,35 @@ def main(argv=None):
                    "q": q, "admm_iters": iters, "lambda": lam,
                    "l2": "inputs larger than L2 (A = 800 MB)",
                    "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "alu", "achieved": achieved_tf,
-                     "peak": ffma_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / ffma_peak, "traffic": None,
-                     "kernel": "k_prod (A X and A^T Y, FP32 FFMA)",
-                     "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 x "
-                                    f"{peaks['sm_max_mhz']:.0f} MHz",
-                     "hbm_gbs": achieved_gbs, "hbm_peak_gbs": peaks["hbm"],
-                     "hbm_frac": achieved_gbs / peaks["hbm"],
-                     "hbm_peak_source": peaks["src"],
-                     "ms_per_pass": pass_ms},
+        "roofline": {"bound": "hbm", "achieved": admm_gbs,
+                     "peak": peaks["hbm"], "unit": "GB/s",
+                     "frac": admm_gbs / peaks["hbm"], "traffic": traffic,
+                     "kernel": f"k_admm_fast ({iters} sweeps, one launch)",
+                     "algorithmic_bytes": admm_bytes,
+                     "peak_source": peaks["src"] + " (copy bandwidth)",
+                     "note": "latency-bound: two grid barriers and two r x r "
+                             "solves per sweep; the working set stays in "
+                             "shared memory and L2"},
+        "roofline_sketch": {"bound": "hbm", "achieved": sketch_gbs,
+                            "peak": peaks["hbm"], "unit": "GB/s",
+                            "frac": sketch_gbs / peaks["hbm"],
+                            "traffic": _traffic("k_tc_prod", 1),
+                            "traffic_note": "product kernels only; pack "
+                                            "and fix-up read L2-resident "
+                                            "panels",
+                            "kernel": "cnmf_sketch_pass: k_pack_panel + "
+                                      "k_tc_prod (3xTF32 tcgen05) + "
+                                      "k_prod_fixup, A X and A^T Y",
+                            "algorithmic_bytes": bytes_pass,
+                            "ms_per_pass": pass_ms},
         "clocks": clk.summary(),
         "breakdown": breakdown,
         "gpu_launches": launches_per_step(q) * args.steps,
+        "gpu_launches_note": "library kernels per step: 2 Gaussian panels, "
+                             "per pass 2 x (pack, product, fix-up) + "
+                             "CholeskyQR2 (gram, finish, apply, finish, "
+                             "apply), A-check product, cross product (2), "
+                             "one ADMM launch",
     }
 
     # ---- end to end through the public API with host buffers
