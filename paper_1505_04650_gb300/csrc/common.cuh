@@ -102,41 +102,55 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 // ---------------------------------------------------------------------------
 // Grid barrier for a cooperative (co-resident) grid, with a bounded wait.
-// bar[0] = arrival count, bar[1] = generation, bar[2] = abort flag.
-// Returns false when the grid must stop (timeout here or elsewhere); the
-// timeout sets CNMF_E_TIMEOUT in *status and raises the abort flag, so every
-// other CTA leaves its own wait promptly instead of spinning to its limit.
+// bar[0] counts arrivals since the launch (the caller zeroes it before the
+// launch); bit 31 is the abort flag.  Arrival k of a CTA is ticket
+// t = atomicAdd(bar, 1); the barrier it belongs to opens when the count
+// reaches (t / G + 1) G, G the number of CTAs, so nothing is ever reset and
+// the only round trips on the critical path are the last arrival's add and
+// the waiters' next poll.  Returns false when the grid must stop (timeout
+// here or elsewhere); the timeout sets CNMF_E_TIMEOUT in *status and raises
+// the abort bit, so every other CTA leaves its own wait promptly.
 // ---------------------------------------------------------------------------
+constexpr unsigned GRID_ABORT = 0x80000000u;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int32_t* status,
                                              uint64_t timeout_ns) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vbar = bar;
-    int ok = vbar[2] == 0;
-    if (ok) {
-      unsigned gen = vbar[1];
-      __threadfence();
-      unsigned arrived = atomicAdd(&bar[0], 1u);
-      if (arrived == gridDim.x * gridDim.y - 1) {
-        bar[0] = 0;
-        __threadfence();
-        atomicExch(&bar[1], gen + 1u);
-      } else {
-        uint64_t t0 = globaltimer_ns();
-        unsigned spins = 0;
-        while (vbar[1] == gen) {
-          if (vbar[2] != 0) { ok = 0; break; }
-          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+    int ok = 1;
+    const unsigned G = gridDim.x * gridDim.y;
+    __threadfence();   // this CTA's writes (ordered by the barrier above)
+    const unsigned t = atomicAdd(&bar[0], 1u);
+    if (t & GRID_ABORT) {
+      ok = 0;
+    } else {
+      const unsigned target = (t / G + 1u) * G;
+      uint64_t t0 = 0;
+      unsigned spins = 0;
+      for (;;) {
+        const unsigned v = ld_acquire_gpu(&bar[0]);
+        if (v & GRID_ABORT) { ok = 0; break; }
+        if (v >= target) break;
+        if ((++spins & 63u) == 0) {
+          const uint64_t now = globaltimer_ns();
+          if (t0 == 0) t0 = now;
+          else if (now - t0 > timeout_ns) {
             set_status(status, CNMF_E_TIMEOUT);
-            atomicExch(&bar[2], 1u);
+            atomicOr(&bar[0], GRID_ABORT);
             ok = 0;
             break;
           }
         }
       }
-      __threadfence();
     }
+    __threadfence();
     ok_s = ok;
   }
   __syncthreads();
