@@ -32,6 +32,7 @@ import numpy as np
 __all__ = [
     "CONFIGS", "lowrank", "separable", "init_factors", "gaussian",
     "as_storage", "bf16_round", "widen", "lowrank_torch", "init_torch",
+    "separable_torch",
 ]
 
 # Workload shapes: a small FP64 case, the large FP32 case, the wide separable
@@ -194,3 +195,30 @@ def init_torch(m: int, n: int, r: int, seed: int, device="cuda"):
     U0 = torch.rand(m, r, generator=g, device=device)
     V0 = torch.rand(r, n, generator=g, device=device)
     return U0, V0.t().contiguous()
+
+
+def separable_torch(m: int, n: int, r: int, sigma: float, seed: int,
+                    device="cuda"):
+    """The separable recipe drawn with PyTorch's generator on `device`
+    (X0, then the Exp(1) draws of H, then the permutation, then the noise;
+    FP32): A = X0 [I_r | H] Pi + |N(0, sigma^2)| with A[:, perm[j]] equal to
+    column j of X0 [I_r | H].  Returns (A, anchors = perm[:r]) on `device`."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    X0 = torch.rand(m, r, generator=g, device=device)
+    E = torch.empty(r, n - r, device=device).exponential_(1.0, generator=g)
+    H = E / E.sum(dim=0, keepdim=True)
+    perm = torch.randperm(n, generator=g, device=device)
+    W = torch.cat([torch.eye(r, device=device), H], dim=1)
+    Wp = torch.empty_like(W)
+    Wp[:, perm] = W
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        A = X0 @ Wp
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    if sigma > 0:
+        A += torch.randn(m, n, generator=g, device=device).abs_() * sigma
+    return A, perm[:r].clone()

@@ -41,3 +41,16 @@ def unit(storage: str) -> float:
 
 def rel(a, b) -> float:
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def product_bound(storage, s):
+    """Relative bound (times |A| |B|) of a length-s product with A stored
+    as `storage`: FP64 -> (s + 2) u; FP32 and BF16 run on the tensor cores
+    with FP32 accumulation (2u per add) plus the operand-split residual
+    (3xTF32: 2^-19; bf16 hi + lo of the thin operand: 2^-17)."""
+    u = unit(storage)
+    if storage == "bf16":
+        return (s + 2) * 2 * u + 2.0 ** -17
+    if storage == "f32":
+        return (s + 2) * 2 * u + 2.0 ** -19
+    return (s + 2) * u

@@ -18,7 +18,7 @@ from oracle import compress as ocomp
 from oracle import philox as ophil
 from oracle import residual as ores
 
-from gpu_util import need_gpu, rel, to_dev, to_np, unit, wdt
+from gpu_util import need_gpu, product_bound, rel, to_dev, to_np, unit, wdt
 
 pytestmark = pytest.mark.gpu
 
@@ -51,16 +51,6 @@ CASES = [  # m, n, k  (n % 4 == 0: FP32 rows 16-byte aligned, tensor cores)
     (1, 1, 1), (37, 53, 5), (300, 257, 30), (129, 4100, 16), (5000, 33, 20),
     (640, 700, 60), (200, 300, 80), (150, 170, 128), (1000, 1028, 30),
     (257, 516, 128), (4100, 260, 48), (3, 8, 2)]
-
-
-def product_bound(storage, s):
-    """(per-add factor, split residual) of the product kernels' bound."""
-    u = unit(storage)
-    if storage == "bf16":
-        return (s + 2) * 2 * u + 2.0 ** -17
-    if storage == "f32":
-        return (s + 2) * 2 * u + 2.0 ** -19
-    return (s + 2) * u
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
