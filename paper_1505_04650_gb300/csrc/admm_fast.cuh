@@ -25,8 +25,8 @@
 
 struct FastSmem {
   int RP, dp, nl;
-  int At, YtT, Xt, M, G, Zx, Zy, E, F, v, Red, sL, sU, sLam, sRt, sVt, sPhit,
-      total;
+  int At, YtT, Xt, M, G, Zx, Zy, E, F, v, mx, Red, sL, sU, sLam, sRt, sVt,
+      sPhit, total;
   // dmax: the register tile width; resident rows are stored zero-padded to
   // dmax with pitch dmax + 4 (4 banks apart: the <= 8 rows one warp reads
   // with 16-byte loads hit distinct banks).
@@ -47,6 +47,7 @@ struct FastSmem {
     E = take(r * RP);
     F = take(r * RP);
     v = take(2 * 32);
+    mx = take(AD_NT / 32);
     Red = take((int64_t)nl * d * r);
     sL = res ? take(mu * dp) : 0;
     sU = res ? take(mu * r) : 0;
@@ -60,13 +61,18 @@ struct FastSmem {
 
 // C[p][4q..4q+3] = init + scale * sum_{s < S} A(p, s) B[s][4q..4q+3]
 // for all tasks (p, q), p < P, q < RP/4; A(p, s) = A[p * sap + s * sas].
+// With `amax`, each warp also writes the largest |C| entry (NaN wins) of
+// its tasks to amax[warp] (every warp writes; the caller syncs).
 template <typename W>
 __device__ __forceinline__ void quad_mm(W* C, int RP, const W* A, int sap,
                                         int sas, const W* B, int P, int S,
                                         W scale, const W* init_g, int init_ld,
                                         int init_cols, W diag, int task0,
-                                        bool init_smem) {
+                                        bool init_smem, W* amax = nullptr,
+                                        bool* nonfinite = nullptr) {
   const int Q = RP / 4;
+  W mx = W(0);
+  bool bad = false;
   for (int t = threadIdx.x - task0; t < P * Q; t += AD_NT) {
     if (t < 0) continue;
     const int p = t / Q, q = t % Q;
@@ -99,9 +105,21 @@ __device__ __forceinline__ void quad_mm(W* C, int RP, const W* A, int sap,
       o[j] += ini[j];
       if (col == p) o[j] += diag;
       if (col >= init_cols) o[j] = W(0);   // keep the padding at zero
-      C[p * RP + col] = o[j];
+      const W av = fabs(o[j]);
+      mx = (av > mx || av != av) ? av : mx;
+      bad |= !isfinite(o[j]);
     }
+    sts4<W>(C + p * RP + 4 * q, o);
   }
+  if (amax) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const W v = __shfl_xor_sync(0xffffffffu, mx, off);
+      mx = (v > mx || v != v) ? v : mx;
+    }
+    if ((threadIdx.x & 31) == 0) amax[threadIdx.x >> 5] = mx;
+  }
+  if (nonfinite && bad) *nonfinite = true;
 }
 
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
@@ -185,53 +203,48 @@ __device__ void store_inverses(W* Zs, int r, int RP, const W* Zx,
   }
 }
 
-// max |E| over n entries, NaN-propagating; every thread gets the result.
-// `red`: 8 entries of shared scratch.  Contains two block barriers.
-template <typename W>
-__device__ W block_max_abs(const W* E, int n, W* red) {
-  auto take = [](W a, W b) { return (b > a || b != b) ? b : a; };
-  W mx = W(0);
-  for (int e = threadIdx.x; e < n; e += AD_NT) mx = take(mx, fabs(E[e]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = take(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  mx = red[0];
-  for (int w = 1; w < AD_NT / 32; ++w) mx = take(mx, red[w]);
-  __syncthreads();
-  return mx;
-}
-
 // -Gm^-1 for the SPD Gm (r x RP, zero padding).  The matrices of Alg. 4's
 // two solves move little from one sweep to the next, so the previous
-// sweep's Z = -Gm_prev^-1 is refined by Newton-Schulz steps: with
-// E = I + Gm Z, Z (I + E) = Z + Z E has residual E^2.  One step when
-// |E| <= tol1, two when |E| <= tol2 (the residual then is below the
-// working precision); otherwise, and on the first sweep, the sweep
-// operator.  Returns the buffer holding the result (Z, F or Gm).  The
-// choice depends only on the data, so every CTA makes the same one.
+// sweep's Z = -Gm_prev^-1 is refined: with E = I + Gm Z, -Gm^-1 =
+// Z (I - E)^-1 = Z (I + E + E^2 + ...), summed by Horner's rule
+// Z_j = Z + Z_{j-1} E (residual E^{j+1}).  The number of terms follows
+// max|E| so that the residual is below the working precision (|E| <= 3e-4:
+// one, <= 5e-3: two, <= 2e-2: three, <= 4e-2: four terms); beyond that, and
+// on the first sweep, the sweep operator.  Returns the buffer holding the
+// result (Z's partner F, E's partner, or Gm).  The choice depends only on
+// the data, so every CTA makes the same one.
 template <typename W, int RMAX>
-__device__ W* refine_or_invert(W* Gm, W* Z, W* E, W* F, W* vbuf, int r,
-                               int RP, bool have, int32_t* status) {
-  const W tol1 = sizeof(W) == 8 ? W(1e-8) : W(3e-4);
-  const W tol2 = sizeof(W) == 8 ? W(1e-4) : W(2e-2);
+__device__ W* refine_or_invert(W* Gm, W* Z, W* E, W* F, W* vbuf, W* wmax,
+                               int r, int RP, bool have, int32_t* status) {
   if (have) {
-    // E = I + Gm Z
-    quad_mm<W>(E, RP, Gm, RP, 1, Z, r, r, W(1), nullptr, 0, r, W(1), 0, false);
+    // E = I + Gm Z, and max |E| per warp into wmax (read by every thread
+    // until the next call: nothing else writes it)
+    quad_mm<W>(E, RP, Gm, RP, 1, Z, r, r, W(1), nullptr, 0, r, W(1), 0, false,
+               wmax);
     __syncthreads();
-    const W e = block_max_abs<W>(E, r * RP, vbuf);
-    if (e <= tol2) {
-      // F = Z + Z E
-      quad_mm<W>(F, RP, Z, RP, 1, E, r, r, W(1), Z, RP, r, W(0), 0, true);
-      __syncthreads();
-      if (e <= tol1) return F;
-      // E = I + Gm F;  Z = F + F E
-      quad_mm<W>(E, RP, Gm, RP, 1, F, r, r, W(1), nullptr, 0, r, W(1), 0,
-                 false);
-      __syncthreads();
-      quad_mm<W>(Z, RP, F, RP, 1, E, r, r, W(1), F, RP, r, W(0), 0, true);
-      __syncthreads();
-      return Z;
+    W e = wmax[0];
+    for (int w = 1; w < AD_NT / 32; ++w)
+      e = (wmax[w] > e || wmax[w] != wmax[w]) ? wmax[w] : e;
+    const bool f64 = sizeof(W) == 8;
+    int terms = 0;
+    if (f64) {
+      terms = e <= W(1e-8) ? 1 : e <= W(2e-6) ? 2 : e <= W(1e-4) ? 3
+              : e <= W(6e-4) ? 4 : 0;
+    } else {
+      terms = e <= W(3e-4) ? 1 : e <= W(5e-3) ? 2 : e <= W(2e-2) ? 3
+              : e <= W(4e-2) ? 4 : 0;
+    }
+    if (terms > 0) {
+      // Gm is free from here on: ping-pong between F and Gm
+      W* cur = Z;
+      W* bufs[2] = {F, Gm};
+      for (int j = 0; j < terms; ++j) {
+        W* nxt = bufs[j & 1];
+        quad_mm<W>(nxt, RP, cur, RP, 1, E, r, r, W(1), Z, RP, r, W(0), 0, true);
+        __syncthreads();
+        cur = nxt;
+      }
+      return cur;
     }
   }
   fast_sweep_inverse<W, RMAX>(Gm, vbuf, r, RP, status);
@@ -266,7 +279,7 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
   W* Zx = sm + o.Zx;
   W* Zy = sm + o.Zy;
   const W* Ix = refine_or_invert<W, RMAX>(G, Zx, sm + o.E, sm + o.F, sm + o.v,
-                                          r, RP, have, a.status);
+                                          sm + o.mx, r, RP, have, a.status);
   mark(1);
   // Xt = M (Yt Yt^T + lam I)^-1 = -M Ix;  Ix kept in Zx
   quad_mm<W>(Xt, RP, M, RP, 1, Ix, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
@@ -281,18 +294,18 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
   __syncthreads();
   mark(3);
   const W* Iy = refine_or_invert<W, RMAX>(G, Zy, sm + o.E, sm + o.F, sm + o.v,
-                                          r, RP, have, a.status);
+                                          sm + o.mx, r, RP, have, a.status);
   mark(4);
-  // Yt^T = M (Xt^T Xt + phi I)^-1 = -M Iy;  Iy kept in Zy
-  quad_mm<W>(YtT, RP, M, RP, 1, Iy, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
+  // Yt^T = M (Xt^T Xt + phi I)^-1 = -M Iy;  Iy kept in Zy; a non-finite
+  // entry of Yt (the chain's last link) flags CNMF_E_NONFINITE
+  bool bad = false;
+  quad_mm<W>(YtT, RP, M, RP, 1, Iy, d, r, W(-1), nullptr, 0, r, W(0), 0, false,
+             nullptr, &bad);
+  if (bad) set_status(a.status, CNMF_E_NONFINITE);
   if (Iy != Zy)
     for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zy[e] = Iy[e];
   __syncthreads();
   mark(5);
-  for (int e = threadIdx.x; e < d * r; e += AD_NT) {
-    const W y = YtT[(e / r) * RP + e % r];
-    if (!isfinite(y)) set_status(a.status, CNMF_E_NONFINITE);
-  }
   mark(6);
 }
 
@@ -442,10 +455,20 @@ __device__ void reduce_fast(const AdmmArgs<W>& a, int with_y0) {
   const int e0 = (int)((c * E) / G), e1 = (int)(((c + 1) * E) / G);
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
   for (int e = e0 + warp; e < e1; e += AD_NT / 32) {
-    W s = W(0);
     const W* p = a.part + e;
-#pragma unroll 4
-    for (int64_t g = lane; g < G; g += 32) s += __ldcg(p + (size_t)g * 3 * dr);
+    // all of this lane's partials in flight at once (G <= 8 * 32 CTAs here;
+    // larger grids take a second round), then added in CTA order
+    W s = W(0);
+    for (int64_t g0 = 0; g0 < G; g0 += 8 * 32) {
+      W v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t g = g0 + lane + 32 * j;
+        v[j] = g < G ? __ldcg(p + (size_t)g * 3 * dr) : W(0);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s += v[j];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {

@@ -49,6 +49,17 @@ __device__ __forceinline__ void lds4<double, double>(const double* p,
   o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
+// Four consecutive W values to shared memory (16-byte aligned address).
+template <typename W>
+__device__ __forceinline__ void sts4(W* p, const W v[4]) {
+  if constexpr (sizeof(W) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+
 // N consecutive W values from shared memory, vectorised when possible.
 template <int N, typename W>
 __device__ __forceinline__ void ldsN(const W* p, W* o) {
