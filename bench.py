@@ -165,10 +165,12 @@ def run_reference(args):
 def launches_per_step(q, chunks_gt1=True):
     """Library kernel launches of one step (compress + one factor launch),
     for FP32 A on the tensor-core product path: each product is a B-panel
-    pack, the product kernel and (split tiles) the fix-up."""
+    pack, the product kernel and (split tiles) the fix-up; between products
+    one CholeskyQR sweep of both panels (gram, finish, apply), CholeskyQR2
+    (gram, finish, apply, finish, apply) after the last pass."""
     prod = 3 if chunks_gt1 else 2
-    per_pass = 2 * prod + 5          # A., A^T., CholeskyQR2 of both panels
-    compress = 2 + (2 * q + 1) * per_pass + prod + 2
+    passes = 2 * q + 1
+    compress = 2 + passes * 2 * prod + (passes - 1) * 3 + 5 + prod + 2
     return compress + 1
 
 
@@ -216,6 +218,8 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the served-stream measurement")
     ap.add_argument("--serving-requests", type=int, default=4096)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the wide-SNMF and mixed-precision lines")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -380,10 +384,10 @@ def main(argv=None):
         "breakdown": breakdown,
         "gpu_launches": launches_per_step(q) * args.steps,
         "gpu_launches_note": "library kernels per step: 2 Gaussian panels, "
-                             "per pass 2 x (pack, product, fix-up) + "
-                             "CholeskyQR2 (gram, finish, apply, finish, "
-                             "apply), A-check product, cross product (2), "
-                             "one ADMM launch",
+                             "per pass 2 x (pack, product, fix-up) + one "
+                             "CholeskyQR sweep (gram, finish, apply), "
+                             "CholeskyQR2 after the last pass (5), A-check "
+                             "product, cross product (2), one ADMM launch",
     }
 
     # ---- end to end through the public API with host buffers
@@ -429,6 +433,9 @@ def main(argv=None):
 
     if not args.no_serving:
         out["serving"] = serving_bench(args.serving_requests)
+    if not args.no_extra:
+        out["snmf_wide"] = snmf_bench(cn, dev)
+        out["mixed_precision"] = mixed_bench(cn, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs, desc = cpu_oracle_sample()
@@ -441,6 +448,66 @@ def main(argv=None):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _time(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def snmf_bench(cn, dev):
+    """Compressed SNMF on the wide separable workload (10000 x 100000,
+    r = 50, d = 60, q = 2, FP32): time of snmf_select (one-sided sketch,
+    R-hat = Q^T A, SPA) and whether the planted anchors came back."""
+    import torch
+    m, n, r, d, q = 10000, 100000, 50, 60, 2
+    A, planted = synth.separable_torch(m, n, r, 1e-3, 1002, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(cn.lib().snmf_select_workspace(m, n, d, 1),
+                     dtype=torch.uint8, device=dev)
+    res = {}
+    ms = _time(lambda: res.update(a=cn.snmf_select(A, r, d, q, 2002, status=st,
+                                                   ws=ws)[0]),
+               5, torch.cuda.current_stream(dev))
+    cn.raise_on_status(st, "snmf bench")
+    ok = sorted(res["a"].cpu().tolist()) == sorted(planted.cpu().tolist())
+    passes = 2 * q + 2          # 2q + 1 sketch products + R-hat
+    return {"workload": "separable 10000 x 100000, r=50, d=60, q=2, fp32",
+            "ms": ms, "anchors_planted": ok,
+            "sketch_gbs": passes * 4.0 * m * n / (ms * 1e-3) / 1e9}
+
+
+def mixed_bench(cn, dev):
+    """Compression of the 50000 x 50000, r = 64 matrix (d = 80, q = 4) with
+    BF16 and FP32 storage: time and algorithmic bytes of A per second."""
+    import torch
+    m = n = 50000
+    r, d, q = 64, 80, 4
+    out = {"workload": "lowrank 50000 x 50000, r=64, d=80, q=4"}
+    for name, dt in (("bf16", torch.bfloat16), ("fp32", torch.float32)):
+        A = synth.lowrank_torch(m, n, r, 0.01, 1003, device=dev).to(dt)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        ws = torch.empty(cn.lib().cnmf_compress_workspace(
+            m, n, d, 2 if name == "bf16" else 1), dtype=torch.uint8, device=dev)
+        ms = _time(lambda: cn.cnmf_compress(A, r, d, q, 2003, status=st, ws=ws),
+                   3, torch.cuda.current_stream(dev))
+        cn.raise_on_status(st, "mixed bench")
+        reads = 2 * (2 * q + 1) + 1
+        out[name] = {"compress_ms": ms,
+                     "gbs": reads * A.element_size() * m * n / (ms * 1e-3) / 1e9}
+        del A, ws
+        torch.cuda.empty_cache()
+    return out
 
 
 def serving_bench(nreq: int):

@@ -5,8 +5,9 @@
 // A^T . Y (m x d -> n x d).  At even t the A-product belongs to the left
 // chain (L: A Omega, A A^T A Omega, ...) and the A^T-product to the right
 // chain (R^T: A^T Psi, ...); at odd t the roles swap.  Every product is
-// re-orthonormalised (CholeskyQR2) before it feeds the next pass, so after
-// pass 2q the m x d panel is L and the n x d panel is R^T.  One more product
+// re-orthonormalised before it feeds the next pass (one shifted CholeskyQR
+// sweep; CholeskyQR2 on the last pass), so after pass 2q the m x d panel
+// is L and the n x d panel is R^T.  One more product
 // gives A-check = A R^T and then A-tilde = L^T A-check (Alg. 4 setup).
 #include <algorithm>
 
@@ -154,8 +155,12 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
     CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
     OrthPanel op[2] = {{zm, m, KP, last ? L : zm, last ? d : KP},
                        {zn, n, KP, last ? Rt : zn, last ? d : KP}};
+    // the last pass gives L and R^T: the unique thin Q (CholeskyQR2); in
+    // between, one sweep keeps the basis well conditioned with the same
+    // span, and the final thin Q does not depend on the basis fed to the
+    // product (it differs by an upper-triangular factor)
     CNMF_TRY(launch_orth(op, 2, d, w, lay.orth_ws, lay.orth_bytes, dev_status,
-                         s));
+                         s, last ? 2 : 1));
     // next pass: A-product takes the n x d panel, A^T-product the m x d one
     X = zn; ldx = KP;
     Y = zm; ldy = KP;

@@ -47,9 +47,13 @@ struct OrthPanel {
   int64_t ldo;
 };
 size_t orth_workspace(int64_t max_rows, int k, cnmf_dtype w);
+// sweeps = 2: CholeskyQR2, the unique thin Q.  sweeps = 1: one shifted
+// CholeskyQR sweep, Q1 = Y R1^-1 -- a well-conditioned basis of the same
+// span that differs from the thin Q by an upper-triangular factor, which
+// the power passes in between final orthonormalisations do not need.
 cnmf_status launch_orth(const OrthPanel* p, int npanels, int k, cnmf_dtype w,
                         void* ws, size_t ws_bytes, int32_t* dev_status,
-                        cudaStream_t s);
+                        cudaStream_t s, int sweeps = 2);
 
 // ---- R^-1 (KP x KP, W-typed, KP = pad_k(k)) of the Cholesky factor of
 //      Y^T Y + shift_abs I (FP64-accurate Gram, FP64 Cholesky) -------------

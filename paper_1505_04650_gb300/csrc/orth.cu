@@ -241,17 +241,21 @@ __device__ __forceinline__ DF df_mul(DF x, DF y) {
   e = fmaf(x.lo, y.hi, e);
   return df_fast(p, e);
 }
+// sqrt and reciprocal: an FP32 seed (the hardware approximations, a few
+// ulps) and one Newton correction from the exactly formed residual, which
+// squares the seed's relative error (Karp and Markstein's scheme).
 __device__ __forceinline__ DF df_sqrt(DF x) {   // x > 0
-  const float r = sqrtf(x.hi);
+  const float y = rsqrtf(x.hi);                 // ~ x^-1/2
+  const float r = x.hi * y;
   const float p = r * r, pe = fmaf(r, r, -p);
   const float res = ((x.hi - p) - pe) + x.lo;   // x - r^2
-  return df_fast(r, res / (2.0f * r));
+  return df_fast(r, res * (0.5f * y));
 }
 __device__ __forceinline__ DF df_rcp(DF y) {
-  const float q = 1.0f / y.hi;
+  const float q = __fdividef(1.0f, y.hi);       // ~ 1 / y
   const DF qy = df_mul(DF{q, 0.0f}, y);
   const DF res = df_add(DF{1.0f, 0.0f}, DF{-qy.hi, -qy.lo});   // 1 - q y
-  return df_fast(q, res.hi / y.hi);
+  return df_fast(q, res.hi * q);
 }
 
 // Arithmetic of the Cholesky factorisation: FP64 for FP64 panels,
@@ -314,9 +318,19 @@ __global__ void __launch_bounds__(OR_NT)
   const bool want = e < KP * KP && (mode == 0 || a <= b) && a < k && b < k;
   double s = 0.0;
   if (want) {
+    // this thread's partials (CTAs sub, sub + FIN_S, ...) all in flight at
+    // once, then added in CTA order
     const double* src = part + (size_t)p * G * KP * KP + e;
-#pragma unroll 4
-    for (int64_t c = sub; c < G; c += FIN_S) s += src[(size_t)c * KP * KP];
+    for (int64_t c0 = sub; c0 < G; c0 += 24 * FIN_S) {
+      double v[24];
+#pragma unroll
+      for (int j = 0; j < 24; ++j) {
+        const int64_t c = c0 + (int64_t)j * FIN_S;
+        v[j] = c < G ? __ldcg(src + (size_t)c * KP * KP) : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < 24; ++j) s += v[j];
+    }
   }
   red[le][sub] = s;
   __syncthreads();
@@ -373,27 +387,43 @@ __global__ void __launch_bounds__(OR_NT)
     R[i] = Ar::from(g);
   }
   __syncthreads();
-  // Right-looking Cholesky, upper factor in place, one barrier per pivot.
-  // Thread 0 owns the pivots: in the phase of pivot j it also finishes the
-  // update of the diagonal entry j + 1 and forms its root and reciprocal,
-  // once.  The other threads update the trailing triangle with the
-  // unscaled row j times 1/R_jj^2 and scale row j - 1, which nobody reads
-  // in this phase.
+  // Right-looking Cholesky, upper factor in place, one barrier per pivot,
+  // with the pivot's reciprocal off the other threads' path: in the phase
+  // of pivot j, warps 0 and 1 both form the update of the diagonal entry
+  // j + 1 (the same arithmetic, so the same value); warp 0 then forms
+  // 1/R_{j+1,j+1}^2, which the next phase's trailing update needs, and
+  // warp 1 the root and its reciprocal, which only the scaling of row j + 1
+  // (one phase later still) needs.  The other warps update the rest of the
+  // trailing triangle with the unscaled row j times 1/R_jj^2; everyone
+  // scales row j - 1, which nobody reads in this phase.
   __shared__ T piv_s[3][3];   // {root, 1/root, 1/root^2}, pivot j in j % 3
-  auto pivot = [&](int j) {
-    T d = R[j * KP + j];
+  auto bad_pivot = [&](T d) {
     const double dl = Ar::lead(d);
     if (!(dl > 0.0) || !isfinite(dl)) {
-      set_status(status, isfinite(dl) ? CNMF_E_CHOLESKY : CNMF_E_NONFINITE);
-      d = Ar::one();
+      if (threadIdx.x == 0)
+        set_status(status, isfinite(dl) ? CNMF_E_CHOLESKY : CNMF_E_NONFINITE);
+      return true;
     }
-    const T rt = Ar::root(d);
-    const T iv = Ar::rcp(rt);
-    piv_s[j % 3][0] = rt;
-    piv_s[j % 3][1] = iv;
-    piv_s[j % 3][2] = Ar::mul(iv, iv);
+    return false;
   };
-  if (threadIdx.x == 0 && k > 0) pivot(0);
+  // warp 0 forms 1/d (lane 0 stores it), warp 1 the root and its
+  // reciprocal; whole warps, so no lane of them waits on a diverged path
+  const int warp = threadIdx.x >> 5;
+  auto pivot_parts = [&](int j, T d) {
+    if (bad_pivot(d)) d = Ar::one();
+    if (warp == 0) {
+      const T iv2 = Ar::rcp(d);
+      if (threadIdx.x == 0) piv_s[j % 3][2] = iv2;
+    } else {
+      const T rt = Ar::root(d);
+      const T iv = Ar::rcp(rt);
+      if (threadIdx.x == 32) {
+        piv_s[j % 3][0] = rt;
+        piv_s[j % 3][1] = iv;
+      }
+    }
+  };
+  if (warp < 2 && k > 0) pivot_parts(0, R[0]);
   __syncthreads();
   // phase j reads slots (j - 1) % 3 and j % 3 and writes (j + 1) % 3
   for (int j = 0; j <= k; ++j) {
@@ -407,14 +437,24 @@ __global__ void __launch_bounds__(OR_NT)
     if (j == k) break;
     const T iv2 = piv_s[j % 3][2];
     const int nt = k - j - 1;
-    // entry (j+1, j+1) is t == 0: thread 0, which then forms pivot j + 1
-    for (int t = threadIdx.x; t < nt * nt; t += OR_NT) {
-      const int ia = j + 1 + t / nt, ib = j + 1 + t % nt;
-      if (ia <= ib)
-        R[ia * KP + ib] =
-            Ar::update(R[ia * KP + ib], R[j * KP + ia], R[j * KP + ib], iv2);
+    if (warp < 2) {
+      if (nt > 0) {
+        // (not stored: the updated entry is only ever the next pivot, and
+        // its slot receives the root when row j + 1 is scaled)
+        const T dn = Ar::update(R[(j + 1) * KP + j + 1], R[j * KP + j + 1],
+                                R[j * KP + j + 1], iv2);
+        pivot_parts(j + 1, dn);
+      }
+    } else {
+      // entries t = 1 .. nt^2 - 1 of the trailing square (t = 0 is the
+      // diagonal entry above) over warps 2 and up
+      for (int t = 1 + threadIdx.x - 64; t < nt * nt; t += OR_NT - 64) {
+        const int ia = j + 1 + t / nt, ib = j + 1 + t % nt;
+        if (ia <= ib)
+          R[ia * KP + ib] =
+              Ar::update(R[ia * KP + ib], R[j * KP + ia], R[j * KP + ib], iv2);
+      }
     }
-    if (threadIdx.x == 0 && nt > 0) pivot(j + 1);
     __syncthreads();
   }
   __syncthreads();
@@ -571,7 +611,7 @@ static void set_smem_attrs() {
 
 template <typename W, int KP>
 static cnmf_status run_orth(const OrthPanel* pp, int np, int k, void* ws,
-                            int32_t* status, cudaStream_t s) {
+                            int32_t* status, cudaStream_t s, int sweeps) {
   set_smem_attrs<W, KP>();
   int64_t maxr = 0;
   for (int i = 0; i < np; ++i) maxr = std::max(maxr, pp[i].rows);
@@ -599,14 +639,21 @@ static cnmf_status run_orth(const OrthPanel* pp, int np, int k, void* ws,
   k_finish<W, KP><<<dim3(nfin, np), OR_NT, fin_smem, s>>>(
       part, G, k, 1, shift, 0.0, gfull, rinv, rinv + KP * KP, 0, tickets, status);
   CNMF_CHECK_LAUNCH();
+  W* q0 = (W*)pp[0].Q;
+  W* q1 = (W*)pp[std::min(1, np - 1)].Q;
+  if (sweeps == 1) {
+    k_apply<W, KP, false><<<grid, OR_NT, ap_smem, s>>>(
+        d[0], d[1], q0, q1, pp[0].ldo, pp[std::min(1, np - 1)].ldo, k, rinv,
+        part);
+    CNMF_CHECK_LAUNCH();
+    return CNMF_OK;
+  }
   k_apply<W, KP, true><<<grid, OR_NT, ap_smem, s>>>(
       d[0], d[1], (W*)d[0].Y, (W*)d[1].Y, d[0].ldy, d[1].ldy, k, rinv, part);
   CNMF_CHECK_LAUNCH();
   k_finish<W, KP><<<dim3(nfin, np), OR_NT, fin_smem, s>>>(
       part, G, k, 1, 0.0, 0.0, gfull, rinv, rinv + KP * KP, 0, tickets, status);
   CNMF_CHECK_LAUNCH();
-  W* q0 = (W*)pp[0].Q;
-  W* q1 = (W*)pp[std::min(1, np - 1)].Q;
   k_apply<W, KP, false><<<grid, OR_NT, ap_smem, s>>>(
       d[0], d[1], q0, q1, pp[0].ldo, pp[std::min(1, np - 1)].ldo, k, rinv,
       part);
@@ -661,15 +708,15 @@ static cnmf_status run_gram_chol(const void* Y, int64_t ld, int64_t rows,
 
 template <typename W>
 static cnmf_status orth_dispatch(const OrthPanel* p, int np, int k, void* ws,
-                                 int32_t* st, cudaStream_t s) {
+                                 int32_t* st, cudaStream_t s, int sw) {
   switch (orth_kp(k)) {
-    case 16: return run_orth<W, 16>(p, np, k, ws, st, s);
-    case 32: return run_orth<W, 32>(p, np, k, ws, st, s);
-    case 48: return run_orth<W, 48>(p, np, k, ws, st, s);
-    case 64: return run_orth<W, 64>(p, np, k, ws, st, s);
-    case 80: return run_orth<W, 80>(p, np, k, ws, st, s);
-    case 96: return run_orth<W, 96>(p, np, k, ws, st, s);
-    default: return run_orth<W, 128>(p, np, k, ws, st, s);
+    case 16: return run_orth<W, 16>(p, np, k, ws, st, s, sw);
+    case 32: return run_orth<W, 32>(p, np, k, ws, st, s, sw);
+    case 48: return run_orth<W, 48>(p, np, k, ws, st, s, sw);
+    case 64: return run_orth<W, 64>(p, np, k, ws, st, s, sw);
+    case 80: return run_orth<W, 80>(p, np, k, ws, st, s, sw);
+    case 96: return run_orth<W, 96>(p, np, k, ws, st, s, sw);
+    default: return run_orth<W, 128>(p, np, k, ws, st, s, sw);
   }
 }
 
@@ -715,12 +762,13 @@ cnmf_status launch_gram_chol(const void* Y, int64_t ld, int64_t rows, int k,
 
 cnmf_status launch_orth(const OrthPanel* p, int np, int k, cnmf_dtype w,
                         void* ws, size_t ws_bytes, int32_t* st,
-                        cudaStream_t s) {
+                        cudaStream_t s, int sweeps) {
   int64_t maxr = 0;
   for (int i = 0; i < np; ++i) maxr = std::max(maxr, p[i].rows);
   if (ws_bytes < orth_workspace(maxr, k, w)) return CNMF_E_WORKSPACE;
-  return w == CNMF_F64 ? orth_dispatch<double>(p, np, k, ws, st, s)
-                       : orth_dispatch<float>(p, np, k, ws, st, s);
+  if (sweeps != 1 && sweeps != 2) return CNMF_E_INVALID_ARG;
+  return w == CNMF_F64 ? orth_dispatch<double>(p, np, k, ws, st, s, sweeps)
+                       : orth_dispatch<float>(p, np, k, ws, st, s, sweeps);
 }
 
 cnmf_status launch_cross(const void* X, int64_t ldx, const void* Y,
@@ -743,3 +791,4 @@ cnmf_status launch_copy2d(const void* src, int64_t lds, void* dst, int64_t ldd,
 }
 
 }  // namespace cnmf
+

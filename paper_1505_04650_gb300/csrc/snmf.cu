@@ -221,19 +221,21 @@ extern "C" cnmf_status snmf_select(const void* A, cnmf_dtype a_type,
   // Q0 = orth(A Omega)
   ProdArgs p0{A, a_type, m, n, lda, false, X, ldx, d, lay.m0, KP, d, dev_status};
   CNMF_TRY(launch_prod(p0, lay.prod_ws, lay.prod_bytes, s));
+  // one CholeskyQR sweep between products, CholeskyQR2 for the final Q
+  // (see cnmf_compress)
   OrthPanel om{lay.m0, m, KP, lay.m0, KP};
   CNMF_TRY(launch_orth(&om, 1, d, w, lay.orth_ws, lay.orth_bytes, dev_status,
-                       s));
+                       s, q == 0 ? 2 : 1));
   OrthPanel on{lay.n0, n, KP, lay.n0, KP};
   for (int j = 0; j < q; ++j) {
     ProdArgs pt{A, a_type, m, n, lda, true, lay.m0, KP, d, lay.n0, KP, d, dev_status};
     CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
     CNMF_TRY(launch_orth(&on, 1, d, w, lay.orth_ws, lay.orth_bytes,
-                         dev_status, s));
+                         dev_status, s, 1));
     ProdArgs pa{A, a_type, m, n, lda, false, lay.n0, KP, d, lay.m0, KP, d, dev_status};
     CNMF_TRY(launch_prod(pa, lay.prod_ws, lay.prod_bytes, s));
     CNMF_TRY(launch_orth(&om, 1, d, w, lay.orth_ws, lay.orth_bytes,
-                         dev_status, s));
+                         dev_status, s, j == q - 1 ? 2 : 1));
   }
   // Rhat^T = A^T Q  (n x d)
   ProdArgs pr{A, a_type, m, n, lda, true, lay.m0, KP, d, lay.rh, KP, d, dev_status};
