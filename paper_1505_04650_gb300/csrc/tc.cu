@@ -11,19 +11,20 @@
 //  * BF16 A (kind::f16): hi, lo are bf16 (|B - hi - lo| <= 2^-18 |B|); A is
 //    used exactly as stored.
 //  * FP32 A (kind::tf32, 3xTF32 split): hi = B rounded to TF32, lo = the FP32
-//    remainder.  The tensor core reads A truncated to TF32 (A_hi); two
-//    converter warps write A_lo = A - A_hi into a second shared-memory tile
-//    and a second MMA adds A_lo B_hi into the hi half.  The dropped terms
-//    (A_lo B_lo and the TF32 truncation of the lo parts) are about 2^-20 of
-//    |A||B|.
+//    remainder.  The tensor core reads A truncated to TF32 (A_hi); four
+//    converter warps write A_lo = A - A_hi into tensor memory (for A^T B
+//    A_hi as well, transposed, since an MN-major TF32 operand is not
+//    usable) and a second MMA, A from TMEM, adds A_lo B_hi into the hi
+//    half.  The dropped terms (A_lo B_lo and the TF32 truncation of the lo
+//    parts) are about 2^-20 of |A||B|.
 //
 // Kernel (one CTA per SM, persistent, stream-K split of (output tile,
 // 128-byte reduction chunk) units like the CUDA-core kernel, sharing its
 // fix-up): warp 0 lane 0 issues TMA loads (128-byte swizzle) into an
 // N-stage mbarrier ring; warp 1 allocates TMEM and lane 0 issues
 // tcgen05.mma (M = 128, N = 2 KP, K = 16 bf16 / 8 tf32, FP32 accumulate)
-// into one of two TMEM accumulators; for FP32 A, warps 2-3 produce A_lo per
-// stage; warps 4-7 drain finished accumulators with
+// into one of two TMEM accumulators; for FP32 A, warps 8-11 produce the
+// TMEM A operands per stage; warps 4-7 drain finished accumulators with
 // tcgen05.ld and write FP32 rows (or split-tile partials).  Every wait is
 // bounded: on expiry the kernel records CNMF_E_TIMEOUT, drains its own
 // copies and MMAs (bounded), frees TMEM and returns.
@@ -40,24 +41,25 @@ namespace cnmf {
 
 constexpr int TC_BM = 128;   // output rows per tile (MMA M)
 
-// Warp roles: 0 TMA, 1 MMA, 2-3 A_lo into shared memory (FP32, A K-major),
-// 4-7 epilogue, 8-11 A_hi / A_lo into tensor memory (FP32, A MN-major).
+// Warp roles: 0 TMA, 1 MMA, 4-7 epilogue, 8-11 (FP32 A) the converters that
+// put A_lo (A K-major) or A_hi and A_lo (A MN-major) into tensor memory.
 template <int KP, bool F32, bool TRANS>
 struct TcCfg {
-  static constexpr bool TMEM_A = F32 && TRANS;      // A operand from TMEM
+  static constexpr bool TMEM_A = F32;               // A operand(s) in TMEM
   static constexpr int NT = TMEM_A ? 384 : 256;
   static constexpr int ESZ = F32 ? 4 : 2;           // bytes per A / B element
   static constexpr int BK = 128 / ESZ;              // reduction per stage
   static constexpr int N = 2 * KP;
   static constexpr int A_BYTES = TC_BM * 128;       // 16 KiB
-  static constexpr int ALO_BYTES = (F32 && !TRANS) ? A_BYTES : 0;
   static constexpr int B_BYTES = N * 128;           // N rows x 128 B
-  static constexpr int STAGE = A_BYTES + ALO_BYTES + B_BYTES;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int ST_FIT = (200 * 1024) / STAGE;
-  // TMEM: NACC accumulators of N columns, then (TMEM_A) per stage BK
-  // columns of A_hi and BK of A_lo.
-  static constexpr int NACC = (!TMEM_A || 512 - 2 * N >= 3 * 2 * BK) ? 2 : 1;
-  static constexpr int ST_TMEM = TMEM_A ? (512 - NACC * N) / (2 * BK) : 8;
+  // TMEM: NACC accumulators of N columns, then (TMEM_A) per stage ACOLS
+  // columns: A_lo (K-major A, whose A_hi the MMA reads from shared
+  // memory), or A_hi and A_lo (MN-major A).
+  static constexpr int ACOLS = TRANS ? 2 * BK : BK;
+  static constexpr int NACC = (!TMEM_A || 512 - 2 * N >= 3 * ACOLS) ? 2 : 1;
+  static constexpr int ST_TMEM = TMEM_A ? (512 - NACC * N) / ACOLS : 8;
   static constexpr int ST_A = ST_FIT < ST_TMEM ? ST_FIT : ST_TMEM;
   static constexpr int STAGES = ST_A > 8 ? 8 : ST_A;
   static constexpr int TMEM_COLS = TMEM_A ? 512
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__((TcCfg<KP, F32, TRANS>::NT), 1)
     for (int i = 0; i < ST; ++i) {
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], 1);
-      mbar_init(&lo_bar[i], TMEM_A ? 4 : 2);
+      mbar_init(&lo_bar[i], 4);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accf_bar[i], 1);
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__((TcCfg<KP, F32, TRANS>::NT), 1)
           break;
         }
         unsigned char* sa = smem + (size_t)stage * C::STAGE;
-        unsigned char* sb = sa + C::A_BYTES + C::ALO_BYTES;
+        unsigned char* sb = sa + C::A_BYTES;
         mbar_expect_tx(&full_bar[stage], (uint32_t)(C::A_BYTES + C::B_BYTES));
         if (!TRANS) {
           tma_load_2d(sa, &tmA, (int)(ts * BK), (int)(tp * TC_BM),
@@ -402,18 +404,18 @@ __global__ void __launch_bounds__((TcCfg<KP, F32, TRANS>::NT), 1)
         }
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + (size_t)stage * C::STAGE);
-        const uint32_t sb = sa + C::A_BYTES + C::ALO_BYTES;
-        if (TMEM_A) {
+        const uint32_t sb = sa + C::A_BYTES;
+        const uint32_t at = tmem + (uint32_t)(C::A_TMEM + stage * C::ACOLS);
+        if (TMEM_A && TRANS) {
           // A_hi . [B_hi | B_lo], then A_lo . B_hi, A from this stage's
           // TMEM columns
-          const uint32_t ahi = tmem + (uint32_t)(C::A_TMEM + stage * 2 * BK);
 #pragma unroll
           for (int kk = 0; kk < BK / MMA_K; ++kk)
-            tc_mma_tf32_ta(dtm, ahi + kk * MMA_K, sdesc(sb + kk * 32, 16, 1024),
+            tc_mma_tf32_ta(dtm, at + kk * MMA_K, sdesc(sb + kk * 32, 16, 1024),
                            IDESC, (ts > ts0 || kk > 0) ? 1u : 0u);
 #pragma unroll
           for (int kk = 0; kk < BK / MMA_K; ++kk)
-            tc_mma_tf32_ta(dtm, ahi + BK + kk * MMA_K,
+            tc_mma_tf32_ta(dtm, at + BK + kk * MMA_K,
                            sdesc(sb + kk * 32, 16, 1024), IDESC_HI, 1u);
           any = true;
         } else {
@@ -430,12 +432,11 @@ __global__ void __launch_bounds__((TcCfg<KP, F32, TRANS>::NT), 1)
           else tc_mma(dtm, ad, bd, IDESC, acc);
           any = true;
         }
-        if (F32) {   // A_lo . B_hi into the hi half (A K-major here)
-          const uint32_t sl = sa + C::A_BYTES;
+        if (F32) {   // A_lo (TMEM) . B_hi into the hi half
 #pragma unroll
           for (int kk = 0; kk < BK / MMA_K; ++kk)
-            tc_mma_tf32(dtm, sdesc(sl + kk * 32, 16, 1024),
-                        sdesc(sb + kk * 32, 16, 1024), IDESC_HI, 1u);
+            tc_mma_tf32_ta(dtm, at + kk * MMA_K, sdesc(sb + kk * 32, 16, 1024),
+                           IDESC_HI, 1u);
         }
         }
         tc_commit(&empty_bar[stage]);
@@ -452,51 +453,16 @@ __global__ void __launch_bounds__((TcCfg<KP, F32, TRANS>::NT), 1)
       while (!mbar_try(&drain_bar, 0) && globaltimer_ns() - t0 < 2000000000ull) {
       }
     }
-  } else if (F32 && !TRANS && (warp == 2 || warp == 3)) {
-    // ---------------- A_lo converter (FP32 A) ----------------
-    // The tensor core reads an FP32 operand as TF32 (the low 13 mantissa
-    // bits ignored); A_lo = A - that value is exact in FP32.  Element-wise
-    // in the same (swizzled) layout, so MN- and K-major tiles alike.
-    const int t = threadIdx.x - 64;
-    int stage = 0;
-    uint32_t phase = 0;
-    int64_t u = u0;
-    bool ok = true;
-    while (ok && u < u1) {
-      const int64_t tp = u / chunks, ts0 = u % chunks;
-      const int64_t ts1 = min(chunks, ts0 + (u1 - u));
-      for (int64_t ts = ts0; ts < ts1; ++ts) {
-        if (!mbar_wait(&full_bar[stage], phase, &abort_s, status)) {
-          ok = false;
-          break;
-        }
-        const float4* src = reinterpret_cast<const float4*>(
-            smem + (size_t)stage * C::STAGE);
-        float4* dst = reinterpret_cast<float4*>(
-            smem + (size_t)stage * C::STAGE + C::A_BYTES);
-#pragma unroll 4
-        for (int i = t; i < C::A_BYTES / 16; i += 64) {
-          float4 v = src[i];
-          v.x -= __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-          v.y -= __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-          v.z -= __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-          v.w -= __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-          dst[i] = v;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&lo_bar[stage]);
-        if (++stage == ST) { stage = 0; phase ^= 1u; }
-      }
-      u = tp * chunks + ts1;
-    }
   } else if (TMEM_A && warp >= 8) {
-    // ---------------- A_hi / A_lo into TMEM (FP32 A, MN-major tile) -------
-    // Warp 8 + w owns TMEM lanes 32 w .. 32 w + 31, i.e. output rows j of
-    // TMA box w.  Lane l reads column j = 32 w + l of the tile (row i of the
-    // box is 128 bytes, 16-byte chunks swizzled by i mod 8), so TMEM lane j
-    // gets row j of A^T: K-major.  A_hi is the FP32 value itself (the tensor
-    // core ignores the low 13 mantissa bits), A_lo = A - A_hi exactly.
+    // ---------------- A operands into TMEM (FP32 A) ----------------
+    // Warp 8 + w owns TMEM lanes 32 w .. 32 w + 31.  The tensor core reads
+    // an FP32 operand as TF32 (the low 13 mantissa bits ignored), so
+    // A_hi = A as stored and A_lo = A - A_hi exactly.
+    //  * K-major tile (A X): lane l takes row i = 32 w + l of the tile, its
+    //    eight 16-byte chunks swizzled by i mod 8, and stores its A_lo row.
+    //  * MN-major tile (A^T Y): lane l reads column j = 32 w + l (row i of
+    //    TMA box w is 128 bytes, chunks swizzled by i mod 8), so TMEM lane j
+    //    gets row j of A^T: A_hi and A_lo, K-major.
     const int w = warp - 8;
     int stage = 0;
     uint32_t phase = 0;
@@ -510,20 +476,37 @@ __global__ void __launch_bounds__((TcCfg<KP, F32, TRANS>::NT), 1)
           ok = false;
           break;
         }
-        const unsigned char* box = smem + (size_t)stage * C::STAGE +
-                                   w * BOX_BYTES + (lane & 3) * 4;
-        uint32_t hi[32], lo[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float v = *reinterpret_cast<const float*>(
-              box + i * 128 + ((((lane >> 2) ^ i) & 7) << 4));
-          hi[i] = __float_as_uint(v);
-          lo[i] = __float_as_uint(v - __uint_as_float(hi[i] & 0xFFFFE000u));
-        }
         const uint32_t ta = tmem + ((uint32_t)(32 * w) << 16) +
-                            (uint32_t)(C::A_TMEM + stage * 2 * BK);
-        tc_st32(ta, hi);
-        tc_st32(ta + BK, lo);
+                            (uint32_t)(C::A_TMEM + stage * C::ACOLS);
+        uint32_t lo[32];
+        if (!TRANS) {
+          const int i = 32 * w + lane;
+          const unsigned char* rowp = smem + (size_t)stage * C::STAGE + i * 128;
+#pragma unroll
+          for (int cch = 0; cch < 8; ++cch) {
+            const float4 v = *reinterpret_cast<const float4*>(
+                rowp + ((cch ^ (i & 7)) << 4));
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              lo[4 * cch + q] = __float_as_uint(
+                  e[q] - __uint_as_float(__float_as_uint(e[q]) & 0xFFFFE000u));
+          }
+          tc_st32(ta, lo);
+        } else {
+          const unsigned char* box = smem + (size_t)stage * C::STAGE +
+                                     w * BOX_BYTES + (lane & 3) * 4;
+          uint32_t hi[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float v = *reinterpret_cast<const float*>(
+                box + i * 128 + ((((lane >> 2) ^ i) & 7) << 4));
+            hi[i] = __float_as_uint(v);
+            lo[i] = __float_as_uint(v - __uint_as_float(hi[i] & 0xFFFFE000u));
+          }
+          tc_st32(ta, hi);
+          tc_st32(ta + BK, lo);
+        }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncwarp();
