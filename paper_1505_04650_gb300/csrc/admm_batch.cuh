@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(AD_NT)
   a.L = (const W*)it.L; a.Rt = (const W*)it.Rt; a.At = (const W*)it.Atilde;
   a.U = (W*)it.U; a.Vt = (W*)it.Vt;
   a.m = it.m; a.n = it.n; a.r = it.r; a.d = it.d;
+  a.Gu = 0;            // every CTA of the cluster sweeps both sides
+  a.Ypub = nullptr;
   const int r = a.r, d = a.d, dr = d * r;
   char* st = (char*)it.state;
   a.Lam = (W*)st;

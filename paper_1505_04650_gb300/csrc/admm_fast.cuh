@@ -30,8 +30,10 @@ struct FastSmem {
   // dmax: the register tile width; resident rows are stored zero-padded to
   // dmax with pitch dmax + 4 (4 banks apart: the <= 8 rows one warp reads
   // with 16-byte loads hit distinct banks).
+  // split: each CTA holds rows of one side only (U/V split), so the two
+  // sides' resident rows share one region.
   __host__ __device__ FastSmem(int r, int d, bool res, int64_t mu,
-                               int64_t nv, int dmax) {
+                               int64_t nv, int dmax, bool split = false) {
     RP = (r + 3) & ~3;
     dp = dmax + 4;
     nl = AD_NT / r;
@@ -49,12 +51,19 @@ struct FastSmem {
     v = take(2 * 32);
     mx = take(AD_NT / 32);
     Red = take((int64_t)nl * d * r);
-    sL = res ? take(mu * dp) : 0;
-    sU = res ? take(mu * r) : 0;
-    sLam = res ? take(mu * r) : 0;
-    sRt = res ? take(nv * dp) : 0;
-    sVt = res ? take(nv * r) : 0;
-    sPhit = res ? take(nv * r) : 0;
+    if (res && split) {
+      const int64_t rows = mu > nv ? mu : nv;
+      sL = sRt = take(rows * dp);
+      sU = sVt = take(rows * r);
+      sLam = sPhit = take(rows * r);
+    } else {
+      sL = res ? take(mu * dp) : 0;
+      sU = res ? take(mu * r) : 0;
+      sLam = res ? take(mu * r) : 0;
+      sRt = res ? take(nv * dp) : 0;
+      sVt = res ? take(nv * r) : 0;
+      sPhit = res ? take(nv * r) : 0;
+    }
     total = o;
   }
 };
@@ -253,12 +262,15 @@ __device__ W* refine_or_invert(W* Gm, W* Z, W* E, W* F, W* vbuf, W* wmax,
 
 // SX, SY^T: the reduced shares (global memory written by other CTAs, read
 // through L2, or this CTA's shared memory when sxy_smem).
-// have: Zx, Zy hold the previous sweep's inverses.
+// have: Zx, Zy hold the previous sweep's inverses.  half: stop after the
+// X update (U-side CTAs of the split).  ypub: where to publish Yt^T
+// (d x RP) for the U-side CTAs, or null.
 template <typename W, int RMAX>
 __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
                            bool have, uint64_t* sub = nullptr,
                            const W* SXp = nullptr, const W* SYp = nullptr,
-                           bool sxy_smem = false) {
+                           bool sxy_smem = false, bool half = false,
+                           W* ypub = nullptr) {
   if (!SXp) { SXp = a.SX; SYp = a.SY; }
   const int r = a.r, d = a.d, RP = o.RP, Q = RP / 4;
   uint64_t tm = sub ? globaltimer_ns() : 0;
@@ -287,6 +299,7 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
     for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zx[e] = Ix[e];
   __syncthreads();
   mark(2);
+  if (half) return;
   // M = SY^T + At^T Xt (d x RP);  G = Xt^T Xt + phi I
   quad_mm<W>(M, RP, At, 1, d, Xt, d, d, W(1), SYp, r, r, W(0), 0, sxy_smem);
   quad_mm<W>(G, RP, Xt, 1, RP, Xt, r, d, W(1), nullptr, 0, r, a.phi,
@@ -306,7 +319,29 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
     for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zy[e] = Iy[e];
   __syncthreads();
   mark(5);
+  if (ypub)
+    for (int e = threadIdx.x; e < d * RP; e += AD_NT) ypub[e] = YtT[e];
   mark(6);
+}
+
+// Rows of `side` (0: U / L rows, 1 and 2: V / R^T rows) that CTA c of G
+// owns: part c of G, or with the U/V split (a.Gu > 0) part c of Gu on the
+// U side and part c - Gu of G - Gu on the V side (false: none).
+template <typename W>
+__device__ __forceinline__ bool side_rows(const AdmmArgs<W>& a, int side,
+                                          int64_t G, int64_t c, int64_t& i0,
+                                          int64_t& i1) {
+  const bool vside = side > 0;
+  const int64_t tot = vside ? a.n : a.m;
+  int64_t gg = G, cc = c;
+  if (a.Gu > 0) {
+    if (vside != (c >= a.Gu)) return false;
+    gg = vside ? G - a.Gu : a.Gu;
+    cc = vside ? c - a.Gu : c;
+  }
+  i0 = (cc * tot) / gg;
+  i1 = ((cc + 1) * tot) / gg;
+  return true;
 }
 
 // Thread (l, b): column b of Xt (U side) or Yt^T (V side) in registers;
@@ -331,8 +366,8 @@ __device__ void sweep_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
   W* Red = sm + o.Red;
   for (int side = 0; side < 2 + (mode == 0 ? 1 : 0); ++side) {
     const bool vside = side > 0;
-    const int64_t tot = vside ? a.n : a.m;
-    const int64_t i0 = (c * tot) / G, i1 = ((c + 1) * tot) / G;
+    int64_t i0, i1;
+    if (!side_rows(a, side, G, c, i0, i1)) continue;   // uniform per CTA
     const W* rows = RES ? sm + (vside ? o.sRt : o.sL) : (vside ? a.Rt : a.L);
     const int64_t rstride = RES ? dp : d;
     W* P = RES ? sm + (vside ? o.sVt : o.sU) : (vside ? a.Vt : a.U);
@@ -415,8 +450,8 @@ __device__ void fast_resident_copy(const AdmmArgs<W>& a, W* sm,
   const int r = a.r, d = a.d, dp = o.dp;  // rows padded with zeros to dp
   const int64_t G = gridDim.x, c = blockIdx.x;
   for (int side = 0; side < 2; ++side) {
-    const int64_t tot = side ? a.n : a.m;
-    const int64_t i0 = (c * tot) / G, i1 = ((c + 1) * tot) / G;
+    int64_t i0, i1;
+    if (!side_rows(a, side, G, c, i0, i1)) continue;
     const int64_t nr = i1 - i0;
     W* rs = sm + (side ? o.sRt : o.sL);
     const W* rg = side ? a.Rt : a.L;
@@ -456,15 +491,21 @@ __device__ void reduce_fast(const AdmmArgs<W>& a, int with_y0) {
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
   for (int e = e0 + warp; e < e1; e += AD_NT / 32) {
     const W* p = a.part + e;
-    // all of this lane's partials in flight at once (G <= 8 * 32 CTAs here;
-    // larger grids take a second round), then added in CTA order
+    // the CTAs holding rows of this entry's side
+    int64_t gs = 0, ge = G;
+    if (a.Gu > 0) {
+      if (e < dr) ge = a.Gu;
+      else gs = a.Gu;
+    }
+    // all of this lane's partials in flight at once (8 * 32 CTAs per
+    // round), then added in CTA order
     W s = W(0);
-    for (int64_t g0 = 0; g0 < G; g0 += 8 * 32) {
+    for (int64_t g0 = gs; g0 < ge; g0 += 8 * 32) {
       W v[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int64_t g = g0 + lane + 32 * j;
-        v[j] = g < G ? __ldcg(p + (size_t)g * 3 * dr) : W(0);
+        v[j] = g < ge ? __ldcg(p + (size_t)g * 3 * dr) : W(0);
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) s += v[j];
@@ -486,9 +527,15 @@ template <typename W, int DMAX, int RMAX, bool RES>
 __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* sm = reinterpret_cast<W*>(smem_raw);
-  const FastSmem o(a.r, a.d, RES, a.mu, a.nv, DMAX);
+  const FastSmem o(a.r, a.d, RES, a.mu, a.nv, DMAX, a.Gu > 0);
   const int r = a.r, d = a.d, RP = o.RP;
-  const bool prof = a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0;
+  // with the U/V split: U-side CTAs stop after the X update; the first
+  // V-side CTA (which has everything) publishes Yt^T, keeps the state and
+  // is the one profiled
+  const bool uside = a.Gu > 0 && (int)blockIdx.x < a.Gu;
+  const int lead = a.Gu > 0 ? a.Gu : 0;
+  const size_t ypsz = (size_t)d * RP;
+  const bool prof = a.phase_ns && (int)blockIdx.x == lead && threadIdx.x == 0;
   uint64_t tph[5] = {0, 0, 0, 0, 0};
   uint64_t tsub[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int e = threadIdx.x; e < d * d; e += AD_NT) sm[o.At + e] = a.At[e];
@@ -514,7 +561,16 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   __syncthreads();
   for (int it = 0; it < a.iters; ++it) {
     uint64_t t0 = prof ? globaltimer_ns() : 0;
-    small_fast<W, RMAX>(a, sm, o, have0 || it > 0, prof ? tsub : nullptr);
+    if (uside && it > 0) {   // Yt^T of this sweep, from the V side
+      const W* yp = a.Ypub + (size_t)(it & 1) * ypsz;
+      for (int e = threadIdx.x; e < d * RP; e += AD_NT) sm[o.YtT + e] = __ldcg(yp + e);
+      __syncthreads();
+    }
+    small_fast<W, RMAX>(a, sm, o, have0 || it > 0, prof ? tsub : nullptr,
+                        nullptr, nullptr, false, uside,
+                        (a.Gu > 0 && (int)blockIdx.x == lead)
+                            ? a.Ypub + (size_t)((it + 1) & 1) * ypsz
+                            : nullptr);
     uint64_t t1 = prof ? globaltimer_ns() : 0;
     sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 7 : nullptr,
                              gridDim.x, blockIdx.x,
@@ -532,7 +588,7 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
     }
   }
   if (RES) fast_resident_copy<W>(a, sm, o, 1);
-  if (blockIdx.x == 0) {
+  if ((int)blockIdx.x == lead) {
     for (int e = threadIdx.x; e < d * r; e += AD_NT) {
       const int k = e / r, bb = e % r;
       a.Yt[bb * d + k] = sm[o.YtT + k * RP + bb];

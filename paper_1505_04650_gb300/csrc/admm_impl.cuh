@@ -66,6 +66,12 @@ struct AdmmArgs {
   double* phase_ns;   // optional: CTA 0's time per phase, summed over sweeps
   int phase_ns_len;
   int64_t mu, nv;     // max rows per CTA on the U side / V side
+  // Side split of the fast kernel (0: every CTA sweeps rows of both
+  // sides): CTAs [0, Gu) own U rows, [Gu, G) own V rows.  U-side CTAs
+  // stop the small algebra after the X update and read Yt^T, which the
+  // first V-side CTA publishes in Ypub (two buffers, by sweep parity).
+  int Gu;
+  W* Ypub;
 };
 
 struct AdmmSmem {
@@ -393,15 +399,35 @@ inline size_t factor_ws(int r, int d, size_t e, int G) {
   cv.take<char>((size_t)r * d * e);
   cv.take<char>((size_t)G * 3 * d * r * e);
   cv.take<unsigned>(64);
+  cv.take<char>((size_t)2 * d * ((r + 3) & ~3) * e);   // Ypub
   return cv.off;
 }
 
 struct AdmmPlan {
-  int G;
+  int G, Gu;
   const void* fn;
   size_t smem;
   int64_t mu, nv;
 };
+
+// U/V split of the fast kernel's CTAs.  A U-side CTA stops the small
+// algebra after the X update, so it starts its rows earlier than a V-side
+// CTA by the second half of the chain (dt, about 3.5 us on GB300); rows
+// cost about 4e-5 d r us each.  Gu balances m / Gu row costs against
+// dt + n / (G - Gu) row costs.
+inline int split_gu(int64_t m, int64_t n, int r, int d, int G) {
+  if (G < 2) return 0;
+  const double c = 4e-5 * d * r, dt = 3.5;
+  int best = 0;
+  double bt = 1e300;
+  for (int gu = 1; gu < G; ++gu) {
+    const double tu = (double)((m + gu - 1) / gu) * c;
+    const double tv = dt + (double)((n + (G - gu) - 1) / (G - gu)) * c;
+    const double t = tu > tv ? tu : tv;
+    if (t < bt) { bt = t; best = gu; }
+  }
+  return best;
+}
 
 // Opt-in shared memory left for a kernel's dynamic buffer (set once).
 inline size_t admm_limit(const void* fn) {
@@ -431,7 +457,7 @@ inline bool coop_ok(const void* fn, size_t smem) {
 template <typename W, int DMAX, int RMAX, bool RES>
 static bool plan_fast(AdmmPlan& P, int r, int d) {
   const void* fn = (const void*)k_admm_fast<W, DMAX, RMAX, RES>;
-  FastSmem o(r, d, RES, P.mu, P.nv, DMAX);
+  FastSmem o(r, d, RES, P.mu, P.nv, DMAX, P.Gu > 0);
   const size_t smem = (size_t)o.total * sizeof(W);
   if (smem > admm_limit(fn) || !coop_ok(fn, smem)) return false;
   P.fn = fn;
@@ -443,8 +469,9 @@ template <typename W>
 static bool admm_plan(AdmmPlan& P, int64_t m, int64_t n, int r, int d) {
   P.G = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(m + n, AD_BR)),
                                (int64_t)num_sms());
-  P.mu = ceil_div(m, P.G);
-  P.nv = ceil_div(n, P.G);
+  P.Gu = split_gu(m, n, r, d, P.G);
+  P.mu = P.Gu ? ceil_div(m, P.Gu) : ceil_div(m, P.G);
+  P.nv = P.Gu ? ceil_div(n, P.G - P.Gu) : ceil_div(n, P.G);
   if (r <= 16 && d <= 32) {
     if (plan_fast<W, 32, 16, true>(P, r, d)) return true;
     if (plan_fast<W, 32, 16, false>(P, r, d)) return true;
@@ -459,6 +486,9 @@ static bool admm_plan(AdmmPlan& P, int64_t m, int64_t n, int r, int d) {
   }
   const void* fn = (const void*)k_admm<W>;
   AdmmSmem o(r, d);
+  P.Gu = 0;
+  P.mu = ceil_div(m, P.G);
+  P.nv = ceil_div(n, P.G);
   P.smem = (size_t)o.total * sizeof(W);
   P.fn = fn;
   return P.smem <= admm_limit(fn) && coop_ok(fn, P.smem);
@@ -482,6 +512,8 @@ static cnmf_status run_factor(const void* L, const void* Rt, const void* At,
   a.SY = cv.take<W>((size_t)r * d);
   a.part = cv.take<W>((size_t)G * 3 * d * r);
   a.bar = cv.take<unsigned>(64);
+  a.Ypub = (W*)cv.take<char>((size_t)2 * d * ((r + 3) & ~3) * e);
+  a.Gu = P.Gu;
   char* st = (char*)state;
   a.Lam = (W*)st;
   a.Phit = a.Lam + (size_t)m * r;
