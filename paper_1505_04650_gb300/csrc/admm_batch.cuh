@@ -75,6 +75,28 @@ __global__ void __launch_bounds__(AD_NT)
     sm[o.Xt + e] = W(0);
   }
   __syncthreads();
+  if (!(it.lambda > 0)) {
+    // the balanced default lambda = phi = ||Atilde||_F / r, formed here
+    // (FP64 squares, added in a fixed order) so the caller needs no host
+    // round trip after the compression
+    __shared__ double nrm_s[AD_NT / 32 + 1];
+    double s = 0.0;
+    for (int e = threadIdx.x; e < d * d; e += AD_NT) {
+      const double v = (double)sm[o.At + e];
+      s = fma(v, v, s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) nrm_s[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < AD_NT / 32; ++w) t += nrm_s[w];
+      nrm_s[AD_NT / 32] = sqrt(t) / r;
+    }
+    __syncthreads();
+    a.lam = a.phi = (W)nrm_s[AD_NT / 32];
+  }
 
   // cluster-wide sum of the shares in `buf` (entries [0, E)) in rank order
   auto reduce = [&](int buf, int E) {

@@ -57,7 +57,6 @@ class Request:
     cluster_size: int = 1
     rho: float = math.nan
     floor: float = math.nan
-    floor_uv: tuple | None = None
     nbytes: int = 0
     done_sweeps: int = 0
     problem: BatchProblem | None = None
@@ -210,14 +209,10 @@ class Server:
         rq.cluster_size = self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
 
     def _ready(self, rq: Request, now: float):
-        # penalty: lambda = phi = ||Atilde||_F / r (needs Atilde on host)
+        # penalty: lambda = phi = ||Atilde||_F / r, formed by the batched
+        # kernel itself (lambda <= 0), so nothing waits for the device here
         pb = rq.problem
-        At = pb.Atilde
-        lam = float(torch.linalg.norm(At.double())) / rq.r
-        pb.lam = pb.phi = lam
-        # rank-r truncation of the compressed matrix, lifted back: the
-        # reference point for the request's residual target
-        rq.floor_uv = truncation_factors(pb.L, pb.Rt, At, rq.r)
+        pb.lam = pb.phi = 0.0
         for t in (pb.L, pb.Rt, pb.Atilde, pb.U, pb.Vt, pb.state.buf,
                   pb.scratch, rq.A):
             t.record_stream(self.main)
@@ -232,7 +227,6 @@ class Server:
             rq.Vt = rq.problem.Vt.clone()
         rq.problem = None
         rq.A = None
-        rq.floor_uv = None
 
     def run(self, requests: list[Request], realtime: bool = True) -> dict:
         pending = collections.deque(sorted(requests, key=lambda q: q.t_arrive))
@@ -285,12 +279,18 @@ class Server:
                 running = [rq for rq in running if rq.done_sweeps < rq.iters]
                 outs = []
                 for rq in finished:
-                    outs.append((cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt),
-                                 cnmf_residual(rq.A, *rq.floor_uv)))
+                    outs.append(cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt))
                 self.main.synchronize()   # this round only; compressions go on
                 now = clock()
-                for rq, (res, resf) in zip(finished, outs):
+                for rq in finished:
                     rq.t_done = now
+                # the residual target's reference point (rank-r truncation
+                # of the compressed matrix, lifted back): reporting only,
+                # after the requests are done
+                floors = [cnmf_residual(rq.A, *truncation_factors(
+                    rq.problem.L, rq.problem.Rt, rq.problem.Atilde, rq.r))
+                    for rq in finished]
+                for rq, res, resf in zip(finished, outs, floors):
                     self._finish(rq, res.cpu(), resf.cpu())
                     in_use -= rq.nbytes
                     done.append(rq)

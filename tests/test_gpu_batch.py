@@ -89,3 +89,22 @@ def test_batched_close_to_cooperative_kernel():
     torch.cuda.synchronize()
     assert rel(to_np(pb.U), to_np(U)) <= 1e-4
     assert rel(to_np(pb.Vt), to_np(Vt)) <= 1e-4
+
+
+def test_batched_default_penalty_formed_on_device():
+    """lambda <= 0 in a batch item selects lambda = phi = ||Atilde||_F / r,
+    formed by the kernel: the same trajectory as passing that value."""
+    torch = need_gpu()
+    import paper_1505_04650_gb300 as cn
+    cases = [_case(*s, seed=300 + i) for i, s in enumerate(SHAPES)]
+    explicit = [_problem(torch, cn, c) for c in cases]
+    auto = [_problem(torch, cn, c) for c in cases]
+    for pb in auto:
+        pb.lam = pb.phi = 0.0
+    _, st = cn.cnmf_factor_batched(explicit, 30, cluster_size=2)
+    _, st = cn.cnmf_factor_batched(auto, 30, cluster_size=2, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    for pe, pa in zip(explicit, auto):
+        assert rel(to_np(pa.U), to_np(pe.U)) <= 1e-5
+        assert rel(to_np(pa.Vt), to_np(pe.Vt)) <= 1e-5
