@@ -8,8 +8,10 @@ server
   (bytes of A, the compression panels, factors, state and scratch) and the
   slot count allow;
 * draws each admitted request's synthetic A and compresses it
-  (cnmf_compress) on one of a few side streams, so compression of new
-  requests overlaps the sweeps of running ones;
+  (cnmf_compress) on one of a few side streams, from a pool of host threads
+  (the host-side launch work of a compression runs while the main loop
+  waits for a round), so compression of new requests overlaps the sweeps of
+  running ones;
 * runs the compressed ADMM sweeps of all compressed requests in rounds:
   one batched launch per cluster size (cnmf_factor_batched, replayed from a
   captured CUDA graph) advances every running request by `sweeps_per_round`
@@ -25,8 +27,10 @@ mix.  Latency = completion time - arrival time (host clock).
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import ctypes as C
 import math
+import queue
 import time
 from dataclasses import dataclass
 
@@ -64,6 +68,7 @@ class Request:
     event: torch.cuda.Event | None = None
     stream_idx: int = 0
     keep: bool = False          # keep U, Vt after completion
+    fut: concurrent.futures.Future | None = None
     U: torch.Tensor | None = None
     Vt: torch.Tensor | None = None
 
@@ -126,6 +131,14 @@ class Server:
         self.side = [torch.cuda.Stream(self.dev) for _ in range(compress_streams)]
         self.status = torch.zeros(1, dtype=torch.int32, device=self.dev)
         self.comp_ws = [None] * compress_streams
+        # admission threads, one side stream (and workspace) each at a time
+        self.pool = concurrent.futures.ThreadPoolExecutor(compress_streams)
+        self.free = queue.Queue()
+        for i in range(compress_streams):
+            self.free.put(i)
+        # the synthetic A is drawn with FP32 products; with several admission
+        # threads that setting must not be toggled per call
+        torch.backends.cuda.matmul.allow_tf32 = False
         self.groups: dict[int, dict] = {}
         self.lib = lib()
 
@@ -169,7 +182,9 @@ class Server:
                 g["items"] = save
                 torch.cuda.synchronize(self.dev)
                 graph = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(graph, stream=torch.cuda.Stream(self.dev)):
+                # admission threads keep launching on their streams meanwhile
+                with torch.cuda.graph(graph, stream=torch.cuda.Stream(self.dev),
+                                      capture_error_mode="thread_local"):
                     self._launch(key, g)
                 g["graph"] = graph
                 # the captured launch reads the item array when replayed
@@ -185,27 +200,33 @@ class Server:
             self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
 
     # ---- request lifecycle ----
-    def _admit(self, rq: Request, k: int, now: float):
+    def _admit(self, rq: Request):
+        """Runs on an admission thread: draw A and the initial factors and
+        compress, all on a free side stream."""
         import synth
-        rq.t_admit = now
-        rq.stream_idx = k % len(self.side)
-        s = self.side[rq.stream_idx]
-        with torch.cuda.stream(s):
-            rq.A = synth.lowrank_torch(rq.m, rq.n, rq.r, rq.sigma, rq.seed,
-                                       device=self.dev)
-            U0, Vt0 = synth.init_torch(rq.m, rq.n, rq.r, rq.seed + 1,
-                                       device=self.dev)
-            nb = self.lib.cnmf_compress_workspace(rq.m, rq.n, rq.d, 1)
-            ws = self.comp_ws[rq.stream_idx]
-            if ws is None or ws.numel() < nb:
-                ws = torch.empty(int(nb * 1.25) + 256, dtype=torch.uint8,
-                                 device=self.dev)
-                self.comp_ws[rq.stream_idx] = ws
-            L, Rt, At, _ = cnmf_compress(rq.A, rq.r, rq.d, rq.q, rq.seed + 2,
-                                         status=self.status, ws=ws)
-            rq.problem = BatchProblem(L, Rt, At, U0, Vt0, 1.0, 1.0)
-            rq.event = torch.cuda.Event()
-            rq.event.record(s)
+        slot = self.free.get()
+        try:
+            rq.stream_idx = slot
+            s = self.side[slot]
+            with torch.cuda.stream(s):
+                rq.A = synth.lowrank_torch(rq.m, rq.n, rq.r, rq.sigma, rq.seed,
+                                           device=self.dev)
+                U0, Vt0 = synth.init_torch(rq.m, rq.n, rq.r, rq.seed + 1,
+                                           device=self.dev)
+                nb = self.lib.cnmf_compress_workspace(rq.m, rq.n, rq.d, 1)
+                ws = self.comp_ws[slot]
+                if ws is None or ws.numel() < nb:
+                    ws = torch.empty(int(nb * 1.25) + 256, dtype=torch.uint8,
+                                     device=self.dev)
+                    self.comp_ws[slot] = ws
+                L, Rt, At, _ = cnmf_compress(rq.A, rq.r, rq.d, rq.q,
+                                             rq.seed + 2, status=self.status,
+                                             ws=ws)
+                rq.problem = BatchProblem(L, Rt, At, U0, Vt0, 1.0, 1.0)
+                rq.event = torch.cuda.Event()
+                rq.event.record(s)
+        finally:
+            self.free.put(slot)
         rq.cluster_size = self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
 
     def _ready(self, rq: Request, now: float):
@@ -235,7 +256,6 @@ class Server:
         running: list[Request] = []
         done: list[Request] = []
         in_use = 0
-        k = 0
         rounds = 0
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0
@@ -255,13 +275,14 @@ class Server:
                 waiting.popleft()
                 rq.nbytes = need
                 in_use += need
-                self._admit(rq, k, clock())
-                k += 1
+                rq.t_admit = clock()
+                rq.fut = self.pool.submit(self._admit, rq)
                 compressing.append(rq)
             # compressed requests join the batch at this round
             still = []
             for rq in compressing:
-                if rq.event.query():
+                if rq.fut.done() and rq.fut.result() is None and \
+                        rq.event.query():
                     self._ready(rq, clock())
                     running.append(rq)
                 else:
@@ -295,6 +316,7 @@ class Server:
                     in_use -= rq.nbytes
                     done.append(rq)
             elif compressing:
+                compressing[0].fut.result()
                 compressing[0].event.synchronize()
             elif pending and realtime:
                 time.sleep(max(0.0, min(0.001, pending[0].t_arrive - clock())))
