@@ -230,9 +230,8 @@ def main(argv=None):
     import paper_1505_04650_gb300 as cn
     from paper_1505_04650_gb300 import build as cbuild
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1505_04650_gb300 import replicas
+    world, rank, local = replicas.world()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -286,14 +285,11 @@ def main(argv=None):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        ms = float(t.item())
+    ms = replicas.slowest_ms(ev0.elapsed_time(ev1) / args.steps, dev)
     cn.raise_on_status(st, "bench timed region")
-    value = world * 1000.0 / ms
+    value = replicas.job_rate(1, ms, world)
 
     # ---- phase breakdown (CUDA events, same stream)
     eb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -436,12 +432,9 @@ def main(argv=None):
     ee1.record(stream)
     torch.cuda.synchronize()
     cn.raise_on_status(st, "bench e2e")
-    e2e_ms = ee0.elapsed_time(ee1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    out["e2e"] = {"value": world * 1000.0 / e2e_ms, "unit": "factorizations/s",
+    e2e_ms = replicas.slowest_ms(ee0.elapsed_time(ee1) / args.steps, dev)
+    out["e2e"] = {"value": replicas.job_rate(1, e2e_ms, world),
+                  "unit": "factorizations/s",
                   "h2d_bytes_per_step": int(A_pin.numel() * 4 + U_pin.numel() * 4
                                             + Vt_pin.numel() * 4),
                   "d2h_bytes_per_step": int(U_out.numel() * 4 + Vt_out.numel() * 4),
