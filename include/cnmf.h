@@ -192,7 +192,10 @@ cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type, int64_t m,
  *          resume = 0: Yt <- V R^T, Lam = Phi = 0, k = 0 (Alg. 4 setup).
  *          resume = 1: continue from the state; the result is bitwise the
  *          same as an uninterrupted run.
- *   1 <= r <= d <= 128, r <= 64, lambda, phi > 0.
+ *   1 <= r <= d <= 128, r <= 64, lambda, phi > 0; the per-CTA working set
+ *   of about d^2 + 5 d r + r^2 + 64 (d + r) values of W must fit in shared
+ *   memory (FP32: d = 128 with r <= 32, d = 80 with r = 64; FP64: d = 64
+ *   with r = 32); sizes beyond it return CNMF_E_INVALID_ARG.
  * ---------------------------------------------------------------------- */
 size_t cnmf_factor_workspace(int64_t m, int64_t n, int32_t r, int32_t d,
                              cnmf_dtype w_type);
