@@ -305,15 +305,17 @@ def main(argv=None):
     breakdown = {"compress_ms": eb[0].elapsed_time(eb[1]),
                  "factor_ms": eb[1].elapsed_time(eb[2]),
                  "factor_us_per_sweep": 1e3 * eb[1].elapsed_time(eb[2]) / iters}
-    ph = torch.zeros(16, dtype=torch.float64, device=dev)
+    ph = torch.zeros(20, dtype=torch.float64, device=dev)
     U.copy_(U0)
     Vt.copy_(Vt0)
     cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f,
                    phase_ns=ph)
     torch.cuda.synchronize()
     names = ["small_algebra", "row_sweep", "barrier1", "cta_reduce", "barrier2",
-             "s_grams", "s_inv1", "s_xt", "s_grams2", "s_inv2", "s_yt", "s_check",
-             "w_urows", "w_ured", "w_vrows", "w_vred"]
+             "s_stage", "s_grams_x", "s_solve_x", "s_grams_y", "s_solve_y",
+             "s_publish", "w_urows", "w_ured", "w_vrows", "w_vred",
+             "u_small_algebra", "u_row_sweep", "u_barrier1", "u_cta_reduce",
+             "u_barrier2"]
     breakdown["factor_phase_us_per_sweep"] = {
         k: float(v) / 1e3 / iters for k, v in zip(names, ph.cpu().tolist())}
 

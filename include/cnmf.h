@@ -70,14 +70,18 @@ typedef struct {
   int32_t iters;
   int32_t barrier_timeout_ms; /* 0 -> default (2000 ms) */
   /* Optional device array of phase_ns_len >= 5 doubles (NULL: off).
-   * cnmf_factor adds the nanoseconds CTA 0 spends per phase, summed over
-   * the sweeps: [0] small r x r algebra, [1] row sweep, [2] first grid
-   * barrier, [3] cross-CTA reduction, [4] second grid barrier; with
-   * phase_ns_len >= 12 also the sub-steps of [0] on the register-tiled
-   * path: [5] Grams, [6] first inverse, [7] Xt, [8] second Grams, [9]
-   * second inverse, [10] Yt, [11] finiteness check, [12] U-row updates,
-   * [13] U-side lane sums, [14] V-row updates, [15] V-side lane sums.
-   * Ignored by cnmf_factor_plain. */
+   * cnmf_factor adds the nanoseconds one CTA spends per phase, summed over
+   * the sweeps (CTA 0, or with the register-tiled path's U/V split the
+   * first V-side CTA): [0] small r x r algebra, [1] row sweep, [2] first
+   * grid barrier, [3] cross-CTA reduction, [4] second grid barrier; with
+   * phase_ns_len >= 15 on the register-tiled path also the sub-steps:
+   * [5] staging of the reduced shares, [6] Xt Grams, [7] Xt solve, [8] Yt
+   * Grams, [9] Yt solve, [10] publishing Yt, [11] U-row updates, [12]
+   * U-side lane sums, [13] V-row updates, [14] V-side lane sums; with
+   * phase_ns_len >= 20 and the U/V split, [15..19] the phases [0..4] of
+   * U-side CTA 0; with phase_ns_len >= 20 + 3 G (G CTAs) on that path,
+   * [20 + 3c], [21 + 3c], [22 + 3c] the time CTA c spends in the small
+   * algebra, the row sweep and the first grid barrier.  Ignored by cnmf_factor_plain. */
   double* phase_ns;
   int32_t phase_ns_len;
   int32_t reserved;

@@ -18,7 +18,7 @@ struct BatchSmem {
   FastSmem f;
   int share0, share1, SX, SY, total;
   __host__ __device__ BatchSmem(int r, int d, int dmax)
-      : f(r, d, false, 0, 0, dmax) {
+      : f(r, d, false, 0, 0, dmax, false, false) {
     int o = f.total;
     auto take = [&](int n) { int p = o; o += (n + 3) & ~3; return p; };
     share0 = take(3 * d * r);
@@ -69,7 +69,11 @@ __global__ void __launch_bounds__(AD_NT)
   const int RP = o.RP;
   W* SXs = sm + b.SX;
   W* SYs = sm + b.SY;
-  for (int e = threadIdx.x; e < d * d; e += AD_NT) sm[o.At + e] = a.At[e];
+  for (int e = threadIdx.x; e < d * d; e += AD_NT) {
+    const W v = a.At[e];
+    sm[o.At + e] = v;
+    sm[o.AtT + (e % d) * d + e / d] = v;
+  }
   for (int e = threadIdx.x; e < d * RP; e += AD_NT) {
     sm[o.YtT + e] = W(0);
     sm[o.Xt + e] = W(0);
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(AD_NT)
     __syncthreads();
   }
   for (int s = 0; s < sweeps; ++s) {
-    small_fast<W, RMAX>(a, sm, o, have || s > 0, nullptr, SXs, SYs, true);
+    small_fast<W, DMAX, RMAX>(a, sm, o, have || s > 0, nullptr, SXs, SYs, true);
     const int buf = parity ? b.share1 : b.share0;
     sweep_fast<W, DMAX, false>(a, sm, o, 2, nullptr, CS, rank, sm + buf);
     reduce(buf, 2 * dr);

@@ -4,52 +4,63 @@
 // Layout: every matrix with an r-long dimension is stored with that
 // dimension last and padded to RP = 4 ceil(r / 4) (zeros in the padding),
 // so four consecutive columns are one 16-byte shared-memory load:
-//   At   d x d            Atilde
+//   At, AtT d x d         Atilde and its transpose
 //   YtT  d x RP           Yt^T
 //   Xt   d x RP           Xt
-//   M    d x RP           MX (then MY^T)
-//   G    r x RP           Gram matrix, then -(Gram)^-1
+//   M, T d x RP           MX (then MY^T), solve scratch
+//   G    r x RP           Gram matrix (destroyed by the solve)
+//   Zx, Zy r x RP         kept inverses -(Gram)^-1
+//   E, F, H r x RP        solve scratch
 // Shares of the next sweep's SX = L^T (lam U - Lam) and SY^T =
 // R (phi V - Phi)^T (both d x r) are reduced in that layout.
 //
-// One small-algebra step is six block-wide phases:
-//   M  = SX + At Yt^T            G = Yt Yt^T + lam I        (one phase)
-//   Zx <- -G^-1     (Newton-Schulz from the last sweep's Zx, else the sweep
-//                    operator)
-//   Xt = M (Yt Yt^T + lam I)^-1
-//   M  = SY^T + At^T Xt          G = Xt^T Xt + phi I        (one phase)
-//   Zy <- -G^-1
-//   Yt^T = M (Xt^T Xt + phi I)^-1    (= (G^-1 MY)^T, G symmetric)
-// Each output quad C[p][4q..4q+3] is one thread's task: a length-S loop of
-// one scalar load, one 16-byte load and four FMAs.
+// One small-algebra step is six block-wide phases when the kept inverses
+// need one refinement term:
+//   M  = SX + At Yt^T            G = Yt Yt^T + lam I
+//   T  = -M Zx                   E = I + G Zx
+//   Xt = T + T E                 Zx <- Zx + Zx E
+//   M  = SY^T + At^T Xt          G = Xt^T Xt + phi I
+//   T  = -M Zy                   E = I + G Zy
+//   Yt^T = T + T E               Zy <- Zy + Zy E
+// (Xt = M (Yt Yt^T + lam I)^-1, Yt^T = M (Xt^T Xt + phi I)^-1 = (G^-1
+// MY)^T as G is symmetric.)  Each output quad C[p][4q..4q+3] is one
+// thread's task: a length-S loop of one scalar load, one 16-byte load and
+// four FMAs.
 
 struct FastSmem {
   int RP, dp, nl;
-  int At, YtT, Xt, M, G, Zx, Zy, E, F, v, mx, Red, sL, sU, sLam, sRt, sVt,
-      sPhit, total;
+  int At, AtT, YtT, Xt, M, T, G, Zx, Zy, E, F, H, v, mx, sSX, sSY, Red, sL, sU,
+      sLam, sRt, sVt, sPhit, total;
   // dmax: the register tile width; resident rows are stored zero-padded to
   // dmax with pitch dmax + 4 (4 banks apart: the <= 8 rows one warp reads
   // with 16-byte loads hit distinct banks).
   // split: each CTA holds rows of one side only (U/V split), so the two
   // sides' resident rows share one region.
+  // stage: room to stage the reduced shares SX, SY^T read from global memory.
   __host__ __device__ FastSmem(int r, int d, bool res, int64_t mu,
-                               int64_t nv, int dmax, bool split = false) {
+                               int64_t nv, int dmax, bool split = false,
+                               bool stage = true) {
     RP = (r + 3) & ~3;
     dp = dmax + 4;
     nl = AD_NT / r;
     int o = 0;
     auto take = [&](int64_t n) { int p = o; o += (int)((n + 3) & ~3); return p; };
     At = take(d * d);
+    AtT = take(d * d);
     YtT = take(d * RP);
     Xt = take(d * RP);
     M = take(d * RP);
+    T = take(d * RP);
     G = take(r * RP);
     Zx = take(r * RP);
     Zy = take(r * RP);
     E = take(r * RP);
     F = take(r * RP);
+    H = take(r * RP);
     v = take(2 * 32);
     mx = take(AD_NT / 32);
+    sSX = stage ? take(d * r) : 0;
+    sSY = stage ? take(d * r) : 0;
     Red = take((int64_t)nl * d * r);
     if (res && split) {
       const int64_t rows = mu > nv ? mu : nv;
@@ -119,6 +130,87 @@ __device__ __forceinline__ void quad_mm(W* C, int RP, const W* A, int sap,
       bad |= !isfinite(o[j]);
     }
     sts4<W>(C + p * RP + 4 * q, o);
+  }
+  if (amax) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const W v = __shfl_xor_sync(0xffffffffu, mx, off);
+      mx = (v > mx || v != v) ? v : mx;
+    }
+    if ((threadIdx.x & 31) == 0) amax[threadIdx.x >> 5] = mx;
+  }
+  if (nonfinite && bad) *nonfinite = true;
+}
+
+// One operand pair of dual_mm: C = init + scale * A B + diag I, with
+// A(p, s) = A[p * sap + s * sas] (P rows), B (S x RP), init (P x init_ld,
+// shared memory) or none.  qmaj: consecutive lanes take consecutive rows p
+// of one column quad (pick it when A is read along p, sap = 1: the lanes of a
+// quarter warp then share one 16-byte B load and read consecutive A words);
+// otherwise consecutive lanes take the quads of one row.
+template <typename W>
+struct QProd {
+  W* C;
+  const W* A;
+  int sap, sas;
+  const W* B;
+  int P;
+  W scale;
+  const W* init;
+  int init_ld;
+  W diag;
+  bool qmaj;
+};
+
+// Two products with the same inner length S in one task loop (tasks of x
+// first): every lane runs the same instructions whichever product its task
+// belongs to, so a warp holding tasks of both does not run two loops.  Each
+// output quad is one thread's task.  The padding columns (>= cols) are
+// written as zeros.  amax (y's tasks only): each warp's largest |C| entry
+// (NaN wins) to amax[warp] (every warp writes; the caller syncs).
+// nonfinite: set when an entry of x's output is not finite.
+template <typename W>
+__device__ __forceinline__ void dual_mm(const QProd<W>& x, const QProd<W>& y,
+                                        int RP, int S, int cols,
+                                        W* amax = nullptr,
+                                        bool* nonfinite = nullptr) {
+  const int Q = RP / 4;
+  const int n1 = x.P * Q, n2 = y.P * Q;
+  W mx = W(0);
+  bool bad = false;
+  for (int t = threadIdx.x; t < n1 + n2; t += AD_NT) {
+    const bool sec = t >= n1;
+    const QProd<W>& g = sec ? y : x;
+    const int u = sec ? t - n1 : t;
+    const int p = g.qmaj ? u % g.P : u / Q;
+    const int q = g.qmaj ? u / g.P : u % Q;
+    const W* ap = g.A + p * g.sap;
+    const W* bp = g.B + 4 * q;
+    const int sas = g.sas;
+    W c0 = W(0), c1 = W(0), c2 = W(0), c3 = W(0);
+#pragma unroll 4
+    for (int s = 0; s < S; ++s) {
+      const W av = ap[s * sas];
+      W b4[4];
+      ldsN<4, W>(bp + s * RP, b4);
+      c0 = fma(av, b4[0], c0);
+      c1 = fma(av, b4[1], c1);
+      c2 = fma(av, b4[2], c2);
+      c3 = fma(av, b4[3], c3);
+    }
+    const W sc = g.scale, dg = g.diag;
+    W o[4] = {c0 * sc, c1 * sc, c2 * sc, c3 * sc};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = 4 * q + j;
+      if (g.init && col < cols) o[j] += g.init[p * g.init_ld + col];
+      if (col == p) o[j] += dg;
+      if (col >= cols) o[j] = W(0);   // keep the padding at zero
+      const W av = fabs(o[j]);
+      if (sec) mx = (av > mx || av != av) ? av : mx;
+      else bad |= !isfinite(o[j]);
+    }
+    sts4<W>(g.C + p * RP + 4 * q, o);
   }
   if (amax) {
 #pragma unroll
@@ -212,23 +304,37 @@ __device__ void store_inverses(W* Zs, int r, int RP, const W* Zx,
   }
 }
 
-// -Gm^-1 for the SPD Gm (r x RP, zero padding).  The matrices of Alg. 4's
-// two solves move little from one sweep to the next, so the previous
-// sweep's Z = -Gm_prev^-1 is refined: with E = I + Gm Z, -Gm^-1 =
-// Z (I - E)^-1 = Z (I + E + E^2 + ...), summed by Horner's rule
-// Z_j = Z + Z_{j-1} E (residual E^{j+1}).  The number of terms follows
-// max|E| so that the residual is below the working precision (|E| <= 3e-4:
-// one, <= 5e-3: two, <= 2e-2: three, <= 4e-2: four terms); beyond that, and
-// on the first sweep, the sweep operator.  Returns the buffer holding the
-// result (Z's partner F, E's partner, or Gm).  The choice depends only on
-// the data, so every CTA makes the same one.
+// Xout = M Gm^-1 (P x RP) for the SPD Gm (r x RP, zero padding), with the
+// inverse kept across sweeps.  The matrices of Alg. 4's two solves move
+// little from one sweep to the next, so the previous sweep's Z = -Gm_prev^-1
+// is refined: with E = I + Gm Z, -Gm^-1 = Z (I - E)^-1 = Z (I + E + E^2 +
+// ...).  Both the solution and the new inverse are summed by Horner's rule
+// from the same E:
+//   T = -M Z,   X_j = T + X_{j-1} E,   Z_j = Z + Z_{j-1} E   (X_0 = T,
+//   Z_0 = Z; residual E^{j+1}),
+// so the solve costs one phase (T and E) plus one phase per term, and the
+// product M Gm^-1 needs no phase of its own.  The number of terms follows
+// max|E| so that the residual is below the working precision (FP32: |E| <=
+// 3e-4: one, <= 5e-3: two, <= 2e-2: three, <= 4e-2: four terms); beyond
+// that, and without a kept inverse, the sweep operator inverts Gm and one
+// phase forms Xout = -M (-Gm^-1).  The choice depends only on the data, so
+// every CTA makes the same one.
+// Buffers: M is consumed (the odd Horner steps land there), T, E, F, H are
+// scratch, Gm is destroyed.  The result lands in Xout.  Returns the buffer
+// holding the new inverse: Z itself after the sweep operator (copied during
+// the last phase), else F or H, which the caller copies into Z after the
+// next block barrier and before F or H are written again.  `nonfinite`
+// flags a non-finite entry of Xout.
 template <typename W, int RMAX>
-__device__ W* refine_or_invert(W* Gm, W* Z, W* E, W* F, W* vbuf, W* wmax,
-                               int r, int RP, bool have, int32_t* status) {
+__device__ const W* solve_fast(W* Xout, W* M, W* T, int P, W* Gm, W* Z, W* E,
+                               W* F, W* H, W* vbuf, W* wmax, int r, int RP,
+                               bool have, int32_t* status, bool* nonfinite) {
   if (have) {
-    // E = I + Gm Z, and max |E| per warp into wmax (read by every thread
-    // until the next call: nothing else writes it)
-    quad_mm<W>(E, RP, Gm, RP, 1, Z, r, r, W(1), nullptr, 0, r, W(1), 0, false,
+    // T = -M Z;  E = I + Gm Z (Gm symmetric: read along its columns), and
+    // max |E| per warp into wmax (read by every thread until the next call:
+    // nothing else writes it)
+    dual_mm<W>({T, M, RP, 1, Z, P, W(-1), nullptr, 0, W(0), false},
+               {E, Gm, 1, RP, Z, r, W(1), nullptr, 0, W(1), true}, RP, r, r,
                wmax);
     __syncthreads();
     W e = wmax[0];
@@ -244,84 +350,133 @@ __device__ W* refine_or_invert(W* Gm, W* Z, W* E, W* F, W* vbuf, W* wmax,
               : e <= W(4e-2) ? 4 : 0;
     }
     if (terms > 0) {
-      // Gm is free from here on: ping-pong between F and Gm
-      W* cur = Z;
-      W* bufs[2] = {F, Gm};
-      for (int j = 0; j < terms; ++j) {
-        W* nxt = bufs[j & 1];
-        quad_mm<W>(nxt, RP, cur, RP, 1, E, r, r, W(1), Z, RP, r, W(0), 0, true);
+      const W* xp = T;
+      const W* zp = Z;
+      for (int j = 1; j <= terms; ++j) {
+        // the last step writes Xout; the ones before alternate with M
+        W* xd = ((terms - j) & 1) ? M : Xout;
+        W* zd = (j & 1) ? F : H;
+        dual_mm<W>({xd, xp, RP, 1, E, P, W(1), T, RP, W(0), false},
+                   {zd, zp, RP, 1, E, r, W(1), Z, RP, W(0), false}, RP, r, r,
+                   nullptr, j == terms ? nonfinite : nullptr);
         __syncthreads();
-        cur = nxt;
+        xp = xd;
+        zp = zd;
       }
-      return cur;
+      return zp;
     }
   }
   fast_sweep_inverse<W, RMAX>(Gm, vbuf, r, RP, status);
-  return Gm;
+  quad_mm<W>(Xout, RP, M, RP, 1, Gm, P, r, W(-1), nullptr, 0, r, W(0), 0,
+             false, nullptr, nonfinite);
+  for (int e = threadIdx.x; e < r * RP; e += AD_NT) Z[e] = Gm[e];
+  __syncthreads();
+  return Z;
 }
 
-// SX, SY^T: the reduced shares (global memory written by other CTAs, read
-// through L2, or this CTA's shared memory when sxy_smem).
+// One small-algebra step of Alg. 4 (the Xt and Yt updates).
+// SXp, SYp: the reduced shares -- global memory written by other CTAs
+// (staged into shared memory first, one L2 round trip for both), or this
+// CTA's shared memory when sxy_smem.  ysrc: where to read this sweep's
+// Yt^T (d x RP, global) before starting, or null (it is in YtT already).
 // have: Zx, Zy hold the previous sweep's inverses.  half: stop after the
 // X update (U-side CTAs of the split).  ypub: where to publish Yt^T
 // (d x RP) for the U-side CTAs, or null.
-template <typename W, int RMAX>
+template <typename W, int DMAX, int RMAX>
 __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
                            bool have, uint64_t* sub = nullptr,
                            const W* SXp = nullptr, const W* SYp = nullptr,
                            bool sxy_smem = false, bool half = false,
-                           W* ypub = nullptr) {
+                           W* ypub = nullptr, const W* ysrc = nullptr) {
   if (!SXp) { SXp = a.SX; SYp = a.SY; }
-  const int r = a.r, d = a.d, RP = o.RP, Q = RP / 4;
+  const int r = a.r, d = a.d, RP = o.RP, dr = d * r;
   uint64_t tm = sub ? globaltimer_ns() : 0;
   auto mark = [&](int i) {
     if (sub) { uint64_t t = globaltimer_ns(); sub[i] += t - tm; tm = t; }
   };
   W* At = sm + o.At;
+  W* AtT = sm + o.AtT;
   W* YtT = sm + o.YtT;
   W* Xt = sm + o.Xt;
   W* M = sm + o.M;
+  W* T = sm + o.T;
   W* G = sm + o.G;
-  // M = SX + At Yt^T  (d x RP);  G = Yt Yt^T + lam I  (r x RP)
-  quad_mm<W>(M, RP, At, d, 1, YtT, d, d, W(1), SXp, r, r, W(0), 0, sxy_smem);
-  quad_mm<W>(G, RP, YtT, 1, RP, YtT, r, d, W(1), nullptr, 0, r, a.lam,
-             d * Q, false);
-  __syncthreads();
-  mark(0);
   W* Zx = sm + o.Zx;
   W* Zy = sm + o.Zy;
-  const W* Ix = refine_or_invert<W, RMAX>(G, Zx, sm + o.E, sm + o.F, sm + o.v,
-                                          sm + o.mx, r, RP, have, a.status);
-  mark(1);
-  // Xt = M (Yt Yt^T + lam I)^-1 = -M Ix;  Ix kept in Zx
-  quad_mm<W>(Xt, RP, M, RP, 1, Ix, d, r, W(-1), nullptr, 0, r, W(0), 0, false);
-  if (Ix != Zx)
-    for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zx[e] = Ix[e];
+  W* E = sm + o.E;
+  W* F = sm + o.F;
+  W* H = sm + o.H;
+  constexpr int KS = (DMAX * RMAX + AD_NT - 1) / AD_NT;
+  W vy[KS];
+  if (!sxy_smem) {
+    // SX (and on U-side CTAs this sweep's Yt^T) staged in shared memory
+    // before the X Grams: all loads in flight at once, one L2 round trip.
+    // SY^T: loads issued with them, stored after the X Grams loop.
+    W vx[KS], vp[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int e = threadIdx.x + k * AD_NT;
+      vx[k] = e < dr ? __ldcg(SXp + e) : W(0);
+      vp[k] = (ysrc && e < d * RP) ? __ldcg(ysrc + e) : W(0);
+      vy[k] = (!half && e < dr) ? __ldcg(SYp + e) : W(0);
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int e = threadIdx.x + k * AD_NT;
+      if (e < dr) sm[o.sSX + e] = vx[k];
+      if (ysrc && e < d * RP) YtT[e] = vp[k];
+    }
+    SXp = sm + o.sSX;
+    __syncthreads();
+  }
+  mark(0);
+  // M = SX + At Yt^T  (d x RP, At read along its columns from AtT);
+  // G = Yt Yt^T + lam I  (r x RP)
+  dual_mm<W>({M, AtT, 1, d, YtT, d, W(1), SXp, r, W(0), true},
+             {G, YtT, 1, RP, YtT, r, W(1), nullptr, 0, a.lam, true}, RP,
+             d, r);
+  if (!sxy_smem && !half) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int e = threadIdx.x + k * AD_NT;
+      if (e < dr) sm[o.sSY + e] = vy[k];
+    }
+    SYp = sm + o.sSY;
+  }
   __syncthreads();
+  mark(1);
+  // Xt = M (Yt Yt^T + lam I)^-1
+  const W* zx = solve_fast<W, RMAX>(Xt, M, T, d, G, Zx, E, F, H, sm + o.v,
+                                    sm + o.mx, r, RP, have, a.status, nullptr);
   mark(2);
-  if (half) return;
-  // M = SY^T + At^T Xt (d x RP);  G = Xt^T Xt + phi I
-  quad_mm<W>(M, RP, At, 1, d, Xt, d, d, W(1), SYp, r, r, W(0), 0, sxy_smem);
-  quad_mm<W>(G, RP, Xt, 1, RP, Xt, r, d, W(1), nullptr, 0, r, a.phi,
-             d * Q, false);
+  if (half) {
+    // F, H are next written in the next sweep's solve, after barriers
+    if (zx != Zx)
+      for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zx[e] = zx[e];
+    return;
+  }
+  // M = SY^T + At^T Xt (d x RP);  G = Xt^T Xt + phi I;  the new Zx moves
+  // home before the Y solve writes F, H
+  dual_mm<W>({M, At, 1, d, Xt, d, W(1), SYp, r, W(0), true},
+             {G, Xt, 1, RP, Xt, r, W(1), nullptr, 0, a.phi, true}, RP, d, r);
+  if (zx != Zx)
+    for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zx[e] = zx[e];
   __syncthreads();
   mark(3);
-  const W* Iy = refine_or_invert<W, RMAX>(G, Zy, sm + o.E, sm + o.F, sm + o.v,
-                                          sm + o.mx, r, RP, have, a.status);
-  mark(4);
-  // Yt^T = M (Xt^T Xt + phi I)^-1 = -M Iy;  Iy kept in Zy; a non-finite
+  // Yt^T = M (Xt^T Xt + phi I)^-1 = (G^-1 MY)^T, G symmetric; a non-finite
   // entry of Yt (the chain's last link) flags CNMF_E_NONFINITE
   bool bad = false;
-  quad_mm<W>(YtT, RP, M, RP, 1, Iy, d, r, W(-1), nullptr, 0, r, W(0), 0, false,
-             nullptr, &bad);
+  const W* zy = solve_fast<W, RMAX>(YtT, M, T, d, G, Zy, E, F, H, sm + o.v,
+                                    sm + o.mx, r, RP, have, a.status, &bad);
   if (bad) set_status(a.status, CNMF_E_NONFINITE);
-  if (Iy != Zy)
-    for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zy[e] = Iy[e];
-  __syncthreads();
-  mark(5);
+  mark(4);
+  // the last solve phase ended with a block barrier; Zy, F, H and YtT are
+  // next written or read after further barriers
+  if (zy != Zy)
+    for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zy[e] = zy[e];
   if (ypub)
     for (int e = threadIdx.x; e < d * RP; e += AD_NT) ypub[e] = YtT[e];
-  mark(6);
+  mark(5);
 }
 
 // Rows of `side` (0: U / L rows, 1 and 2: V / R^T rows) that CTA c of G
@@ -535,10 +690,22 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   const bool uside = a.Gu > 0 && (int)blockIdx.x < a.Gu;
   const int lead = a.Gu > 0 ? a.Gu : 0;
   const size_t ypsz = (size_t)d * RP;
+  // profiled: the lead (sub-steps too) and, with the split, U-side CTA 0
   const bool prof = a.phase_ns && (int)blockIdx.x == lead && threadIdx.x == 0;
+  const bool profu = a.phase_ns && a.Gu > 0 && blockIdx.x == 0 &&
+                     threadIdx.x == 0 && a.phase_ns_len >= 20;
+  // with room for it, every CTA's time before and in the first barrier
+  const bool profc = a.phase_ns && threadIdx.x == 0 &&
+                     a.phase_ns_len >= 20 + 3 * (int)gridDim.x;
+  const bool pr = prof || profu || profc;
+  uint64_t tw = 0, tr = 0, tb = 0;
   uint64_t tph[5] = {0, 0, 0, 0, 0};
-  uint64_t tsub[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int e = threadIdx.x; e < d * d; e += AD_NT) sm[o.At + e] = a.At[e];
+  uint64_t tsub[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int e = threadIdx.x; e < d * d; e += AD_NT) {
+    const W v = a.At[e];
+    sm[o.At + e] = v;
+    sm[o.AtT + (e % d) * d + e / d] = v;
+  }
   for (int e = threadIdx.x; e < d * RP; e += AD_NT) {
     sm[o.YtT + e] = W(0);
     sm[o.Xt + e] = W(0);
@@ -560,29 +727,27 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   if (have0) load_inverses<W>(a.Zs, r, RP, sm + o.Zx, sm + o.Zy);
   __syncthreads();
   for (int it = 0; it < a.iters; ++it) {
-    uint64_t t0 = prof ? globaltimer_ns() : 0;
-    if (uside && it > 0) {   // Yt^T of this sweep, from the V side
-      const W* yp = a.Ypub + (size_t)(it & 1) * ypsz;
-      for (int e = threadIdx.x; e < d * RP; e += AD_NT) sm[o.YtT + e] = __ldcg(yp + e);
-      __syncthreads();
-    }
-    small_fast<W, RMAX>(a, sm, o, have0 || it > 0, prof ? tsub : nullptr,
-                        nullptr, nullptr, false, uside,
-                        (a.Gu > 0 && (int)blockIdx.x == lead)
-                            ? a.Ypub + (size_t)((it + 1) & 1) * ypsz
-                            : nullptr);
-    uint64_t t1 = prof ? globaltimer_ns() : 0;
-    sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 7 : nullptr,
+    uint64_t t0 = pr ? globaltimer_ns() : 0;
+    // U-side CTAs read this sweep's Yt^T from the V side
+    small_fast<W, DMAX, RMAX>(
+        a, sm, o, have0 || it > 0, prof ? tsub : nullptr, nullptr, nullptr,
+        false, uside,
+        (a.Gu > 0 && (int)blockIdx.x == lead)
+            ? a.Ypub + (size_t)((it + 1) & 1) * ypsz : nullptr,
+        (uside && it > 0) ? a.Ypub + (size_t)(it & 1) * ypsz : nullptr);
+    uint64_t t1 = pr ? globaltimer_ns() : 0;
+    sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 6 : nullptr,
                              gridDim.x, blockIdx.x,
                              a.part + (size_t)blockIdx.x * 3 * d * r);
-    uint64_t t2 = prof ? globaltimer_ns() : 0;
+    uint64_t t2 = pr ? globaltimer_ns() : 0;
     if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
-    uint64_t t3 = prof ? globaltimer_ns() : 0;
+    uint64_t t3 = pr ? globaltimer_ns() : 0;
     reduce_fast<W>(a, 0);
-    uint64_t t4 = prof ? globaltimer_ns() : 0;
+    uint64_t t4 = pr ? globaltimer_ns() : 0;
     if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
-    if (prof) {
+    if (pr) {
       uint64_t t5 = globaltimer_ns();
+      tw += t1 - t0; tr += t2 - t1; tb += t3 - t2;
       tph[0] += t1 - t0; tph[1] += t2 - t1; tph[2] += t3 - t2;
       tph[3] += t4 - t3; tph[4] += t5 - t4;
     }
@@ -599,7 +764,14 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   }
   if (prof) {
     for (int i = 0; i < 5; ++i) a.phase_ns[i] += (double)tph[i];
-    const int ns = a.phase_ns_len - 5 < 11 ? a.phase_ns_len - 5 : 11;
+    const int ns = a.phase_ns_len - 5 < 10 ? a.phase_ns_len - 5 : 10;
     for (int i = 0; i < ns; ++i) a.phase_ns[5 + i] += (double)tsub[i];
+  }
+  if (profu)
+    for (int i = 0; i < 5; ++i) a.phase_ns[15 + i] += (double)tph[i];
+  if (profc) {
+    a.phase_ns[20 + 3 * blockIdx.x] += (double)tw;
+    a.phase_ns[21 + 3 * blockIdx.x] += (double)tr;
+    a.phase_ns[22 + 3 * blockIdx.x] += (double)tb;
   }
 }

@@ -412,12 +412,14 @@ struct AdmmPlan {
 
 // U/V split of the fast kernel's CTAs.  A U-side CTA stops the small
 // algebra after the X update, so it starts its rows earlier than a V-side
-// CTA by the second half of the chain (dt, about 3.5 us on GB300); rows
-// cost about 4e-5 d r us each.  Gu balances m / Gu row costs against
-// dt + n / (G - Gu) row costs.
+// CTA by the second half of the chain; past a fixed start-up cost that both
+// sides pay, rows cost about 2e-5 d r us each.  Gu balances m / Gu row costs
+// against dt + n / (G - Gu) row costs.  dt = 2.8 us is the measured best on
+// GB300 at m = 20000, n = 10000, d = 30, r = 20 (the Y half itself takes
+// about 3.3 us; the V side's row sweep has a larger fixed cost).
 inline int split_gu(int64_t m, int64_t n, int r, int d, int G) {
   if (G < 2) return 0;
-  const double c = 4e-5 * d * r, dt = 3.5;
+  const double c = 2e-5 * d * r, dt = 2.8;
   int best = 0;
   double bt = 1e300;
   for (int gu = 1; gu < G; ++gu) {
