@@ -311,13 +311,18 @@ def main(argv=None):
     cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f,
                    phase_ns=ph)
     torch.cuda.synchronize()
-    names = ["small_algebra", "row_sweep", "barrier1", "cta_reduce", "barrier2",
+    # slots 3, 4 and 18, 19 (the generic kernel's second and third barrier
+    # phases) stay zero on the register-tiled kernel, whose sweep loop has
+    # no grid barrier: its slot 2 is the reduction with its waits for the
+    # other CTAs' shares
+    names = ["small_algebra", "row_sweep", "reduce_incl_waits", None, None,
              "s_stage", "s_grams_x", "s_solve_x", "s_grams_y", "s_solve_y",
              "s_publish", "w_urows", "w_ured", "w_vrows", "w_vred",
-             "u_small_algebra", "u_row_sweep", "u_barrier1", "u_cta_reduce",
-             "u_barrier2"]
+             "u_small_algebra", "u_row_sweep", "u_reduce_incl_waits", None,
+             None]
     breakdown["factor_phase_us_per_sweep"] = {
-        k: float(v) / 1e3 / iters for k, v in zip(names, ph.cpu().tolist())}
+        k: float(v) / 1e3 / iters for k, v in zip(names, ph.cpu().tolist())
+        if k is not None}
 
     # ---- the sketch products with A (one per side per pass), timed as a
     # pass through the public call: B-panel packing + tensor-core product +

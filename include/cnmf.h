@@ -73,7 +73,10 @@ typedef struct {
    * cnmf_factor adds the nanoseconds one CTA spends per phase, summed over
    * the sweeps (CTA 0, or with the register-tiled path's U/V split the
    * first V-side CTA): [0] small r x r algebra, [1] row sweep, [2] first
-   * grid barrier, [3] cross-CTA reduction, [4] second grid barrier; with
+   * grid barrier, [3] cross-CTA reduction, [4] second grid barrier (the
+   * register-tiled path has no grid barrier in its sweeps: [2] is its
+   * cross-CTA reduction including the waits for the other CTAs' shares,
+   * [3] and [4] stay zero); with
    * phase_ns_len >= 15 on the register-tiled path also the sub-steps:
    * [5] staging of the reduced shares, [6] Xt Grams, [7] Xt solve, [8] Yt
    * Grams, [9] Yt solve, [10] publishing Yt, [11] U-row updates, [12]
@@ -81,7 +84,7 @@ typedef struct {
    * phase_ns_len >= 20 and the U/V split, [15..19] the phases [0..4] of
    * U-side CTA 0; with phase_ns_len >= 20 + 3 G (G CTAs) on that path,
    * [20 + 3c], [21 + 3c], [22 + 3c] the time CTA c spends in the small
-   * algebra, the row sweep and the first grid barrier.  Ignored by cnmf_factor_plain. */
+   * algebra, the row sweep and the reduction with its waits.  Ignored by cnmf_factor_plain. */
   double* phase_ns;
   int32_t phase_ns_len;
   int32_t reserved;

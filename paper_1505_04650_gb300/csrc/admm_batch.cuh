@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(AD_NT)
   a.m = it.m; a.n = it.n; a.r = it.r; a.d = it.d;
   a.Gu = 0;            // every CTA of the cluster sweeps both sides
   a.Ypub = nullptr;
+  a.tpart = a.tsxy = a.typ = nullptr;
   const int r = a.r, d = a.d, dr = d * r;
   char* st = (char*)it.state;
   a.Lam = (W*)st;

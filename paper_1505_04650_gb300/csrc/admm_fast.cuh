@@ -374,20 +374,30 @@ __device__ const W* solve_fast(W* Xout, W* M, W* T, int P, W* Gm, W* Z, W* E,
   return Z;
 }
 
+// Tagged inputs and outputs of one sweep of the cooperative kernel.
+struct SweepIO {
+  const uint64_t* sxy;   // reduced SX then SY^T (2 d r values), or null:
+  uint32_t stag;         //   a.SX, a.SY (plain, after a grid barrier)
+  const uint64_t* yin;   // this sweep's Yt^T (d x RP) for a U-side CTA,
+  uint32_t ytag;         //   or null (YtT holds it)
+  uint64_t* yout;        // where the lead publishes Yt^T, or null
+  uint32_t yotag;
+};
+
 // One small-algebra step of Alg. 4 (the Xt and Yt updates).
 // SXp, SYp: the reduced shares -- global memory written by other CTAs
-// (staged into shared memory first, one L2 round trip for both), or this
-// CTA's shared memory when sxy_smem.  ysrc: where to read this sweep's
-// Yt^T (d x RP, global) before starting, or null (it is in YtT already).
-// have: Zx, Zy hold the previous sweep's inverses.  half: stop after the
-// X update (U-side CTAs of the split).  ypub: where to publish Yt^T
-// (d x RP) for the U-side CTAs, or null.
+// (staged into shared memory first, one L2 round trip for all), or this
+// CTA's shared memory when sxy_smem.  io: the cooperative kernel's tagged
+// shares and Yt^T (null: plain a.SX, a.SY).  have: Zx, Zy hold the previous
+// sweep's inverses.  half: stop after the X update (U-side CTAs of the
+// split).  Returns false when a wait for tagged data gave up (timeout or
+// abort; every thread of the CTA returns the same).
 template <typename W, int DMAX, int RMAX>
-__device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
+__device__ bool small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
                            bool have, uint64_t* sub = nullptr,
                            const W* SXp = nullptr, const W* SYp = nullptr,
                            bool sxy_smem = false, bool half = false,
-                           W* ypub = nullptr, const W* ysrc = nullptr) {
+                           const SweepIO* io = nullptr) {
   if (!SXp) { SXp = a.SX; SYp = a.SY; }
   const int r = a.r, d = a.d, RP = o.RP, dr = d * r;
   uint64_t tm = sub ? globaltimer_ns() : 0;
@@ -407,19 +417,60 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
   W* F = sm + o.F;
   W* H = sm + o.H;
   constexpr int KS = (DMAX * RMAX + AD_NT - 1) / AD_NT;
+  constexpr int NW = sizeof(W) / 4;
   W vy[KS];
   if (!sxy_smem) {
     // SX (and on U-side CTAs this sweep's Yt^T) staged in shared memory
     // before the X Grams: all loads in flight at once, one L2 round trip.
     // SY^T: loads issued with them, stored after the X Grams loop.
     W vx[KS], vp[KS];
+    if (io && io->sxy) {
+      const uint64_t* sx = io->sxy;
+      const uint64_t* sy = io->sxy + (size_t)dr * NW;
+      const uint64_t* yp = io->yin;
+      const uint64_t dx = (uint64_t)io->stag << 32, dy = (uint64_t)io->ytag << 32;
+      uint64_t wx[KS][NW], wy[KS][NW], wp[KS][NW];
 #pragma unroll
-    for (int k = 0; k < KS; ++k) {
-      const int e = threadIdx.x + k * AD_NT;
-      vx[k] = e < dr ? __ldcg(SXp + e) : W(0);
-      vp[k] = (ysrc && e < d * RP) ? __ldcg(ysrc + e) : W(0);
-      vy[k] = (!half && e < dr) ? __ldcg(SYp + e) : W(0);
+      for (int k = 0; k < KS; ++k) {
+        const int e = threadIdx.x + k * AD_NT;
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+          wx[k][h] = e < dr ? ld_relaxed_u64(sx + e * NW + h) : dx;
+          wy[k][h] = (!half && e < dr) ? ld_relaxed_u64(sy + e * NW + h) : dx;
+          wp[k][h] = (yp && e < d * RP) ? ld_relaxed_u64(yp + e * NW + h) : dy;
+        }
+      }
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int e = threadIdx.x + k * AD_NT;
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+          if (e < dr)
+            ok = ok && tag_spin(sx + e * NW + h, io->stag, wx[k][h], a.bar,
+                                a.status, a.timeout_ns);
+          if (!half && e < dr)
+            ok = ok && tag_spin(sy + e * NW + h, io->stag, wy[k][h], a.bar,
+                                a.status, a.timeout_ns);
+          if (yp && e < d * RP)
+            ok = ok && tag_spin(yp + e * NW + h, io->ytag, wp[k][h], a.bar,
+                                a.status, a.timeout_ns);
+        }
+        vx[k] = tag_value<W>(wx[k]);
+        vy[k] = tag_value<W>(wy[k]);
+        vp[k] = tag_value<W>(wp[k]);
+      }
+      if (__syncthreads_or(!ok)) return false;
+    } else {
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int e = threadIdx.x + k * AD_NT;
+        vx[k] = e < dr ? __ldcg(SXp + e) : W(0);
+        vy[k] = (!half && e < dr) ? __ldcg(SYp + e) : W(0);
+        vp[k] = W(0);
+      }
     }
+    const bool ysrc = io && io->yin;
 #pragma unroll
     for (int k = 0; k < KS; ++k) {
       const int e = threadIdx.x + k * AD_NT;
@@ -453,7 +504,7 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
     // F, H are next written in the next sweep's solve, after barriers
     if (zx != Zx)
       for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zx[e] = zx[e];
-    return;
+    return true;
   }
   // M = SY^T + At^T Xt (d x RP);  G = Xt^T Xt + phi I;  the new Zx moves
   // home before the Y solve writes F, H
@@ -474,9 +525,11 @@ __device__ void small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
   // next written or read after further barriers
   if (zy != Zy)
     for (int e = threadIdx.x; e < r * RP; e += AD_NT) Zy[e] = zy[e];
-  if (ypub)
-    for (int e = threadIdx.x; e < d * RP; e += AD_NT) ypub[e] = YtT[e];
+  if (io && io->yout)
+    for (int e = threadIdx.x; e < d * RP; e += AD_NT)
+      tag_put<W>(io->yout + (size_t)e * (sizeof(W) / 4), YtT[e], io->yotag);
   mark(5);
+  return true;
 }
 
 // Rows of `side` (0: U / L rows, 1 and 2: V / R^T rows) that CTA c of G
@@ -505,11 +558,13 @@ __device__ __forceinline__ bool side_rows(const AdmmArgs<W>& a, int side,
 // shares of lam U and phi V, plus Yt0^T = R V^T); mode 1: resume setup;
 // mode 2: ADMM row updates.
 // This CTA is part c of G splitting the rows; its shares go to dst
-// (3 d r entries: SX, SY^T, Yt0^T).
+// (3 d r entries: SX, SY^T, Yt0^T), or with tdst as tagged words (tag) to
+// tdst (2 d r values: SX, SY^T).
 template <typename W, int DMAX, bool RES>
 __device__ void sweep_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
                            int mode, uint64_t* sub, int64_t G, int64_t c,
-                           W* dst) {
+                           W* dst, uint64_t* tdst = nullptr,
+                           uint32_t tag = 0) {
   uint64_t tm = sub ? globaltimer_ns() : 0;
   auto mark = [&](int i) {
     if (sub) { uint64_t t = globaltimer_ns(); sub[i] += t - tm; tm = t; }
@@ -592,7 +647,10 @@ __device__ void sweep_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
         for (int u = 0; u < 8; ++u) t += v[u];
       }
       for (; l < nl; ++l) t += Red[l * dr + e];
-      dst[side * dr + e] = t;
+      if (tdst)
+        tag_put<W>(tdst + (size_t)(side * dr + e) * (sizeof(W) / 4), t, tag);
+      else
+        dst[side * dr + e] = t;
     }
     __syncthreads();
     if (side < 2) mark(2 * side + 1);
@@ -678,6 +736,67 @@ __device__ void reduce_fast(const AdmmArgs<W>& a, int with_y0) {
   }
 }
 
+// The sweep loop's cross-CTA sums: this CTA's slice of the 2 d r entries
+// (SX, then SY^T), one warp per entry, each summed in CTA order over the
+// CTAs holding rows of its side, from sweep it's tagged shares P_it (tag
+// it + 1, buffer it & 1) -- each load waits for its tag, so no grid barrier
+// is needed -- and stored as the reduced shares S_it+1 (tag it + 2, buffer
+// (it + 1) % 3).
+// Buffer reuse.  Every CTA of sweep k + 1 waits (directly, or on the U side
+// through the lead's Yt_k+1) for all of S_k+1, so for every reducer's
+// reading of P_k: two share buffers suffice.  The U side can run one sweep
+// ahead of a V-side CTA (it waits for the lead only), so S_it+1's SX part
+// may be written while that CTA still reads S_it-1: three buffers of S.
+// Returns false when a wait gave up.
+template <typename W>
+__device__ bool reduce_tagged(const AdmmArgs<W>& a, int it) {
+  constexpr int NW = sizeof(W) / 4;
+  const int dr = a.d * a.r, E = 2 * dr;
+  const int64_t G = gridDim.x, c = blockIdx.x;
+  const int e0 = (int)((c * E) / G), e1 = (int)(((c + 1) * E) / G);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const uint32_t tin = (uint32_t)it + 1, tout = (uint32_t)it + 2;
+  const uint64_t* part = a.tpart + (size_t)(it & 1) * G * E * NW;
+  uint64_t* out = a.tsxy + (size_t)((it + 1) % 3) * E * NW;
+  const uint64_t dummy = (uint64_t)tin << 32;
+  bool ok = true;
+  for (int e = e0 + warp; e < e1; e += AD_NT / 32) {
+    int64_t gs = 0, ge = G;
+    if (a.Gu > 0) {
+      if (e < dr) ge = a.Gu;
+      else gs = a.Gu;
+    }
+    W s = W(0);
+    for (int64_t g0 = gs; g0 < ge; g0 += 8 * 32) {
+      uint64_t w[8][NW];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t g = g0 + lane + 32 * j;
+#pragma unroll
+        for (int h = 0; h < NW; ++h)
+          w[j][h] = g < ge ? ld_relaxed_u64(part + ((size_t)g * E + e) * NW + h)
+                           : dummy;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t g = g0 + lane + 32 * j;
+        if (g < ge) {
+#pragma unroll
+          for (int h = 0; h < NW; ++h)
+            ok = ok && tag_spin(part + ((size_t)g * E + e) * NW + h, tin,
+                                w[j][h], a.bar, a.status, a.timeout_ns);
+          s += tag_value<W>(w[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (__all_sync(0xffffffffu, ok) && lane == 0)
+      tag_put<W>(out + (size_t)e * NW, s, tout);
+  }
+  return !__syncthreads_or(!ok);
+}
+
 template <typename W, int DMAX, int RMAX, bool RES>
 __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -713,6 +832,19 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   if (RES) fast_resident_copy<W>(a, sm, o, 0);
   __syncthreads();
 
+  // this CTA's tagged words start at tag 0 (no sweep uses it), so nothing
+  // left by an earlier launch can pass for this launch's data; the setup's
+  // grid barriers order the zeroing before every tagged read
+  constexpr int NW = sizeof(W) / 4;
+  const int E2 = 2 * d * r;
+  const size_t cw = (size_t)E2 * NW;   // one CTA's shares, one parity
+  for (int par = 0; par < 2; ++par)
+    for (size_t e = threadIdx.x; e < cw; e += AD_NT)
+      a.tpart[((size_t)par * gridDim.x + blockIdx.x) * cw + e] = 0;
+  if (blockIdx.x == 0) {
+    for (size_t e = threadIdx.x; e < 3 * cw; e += AD_NT) a.tsxy[e] = 0;
+    for (size_t e = threadIdx.x; e < 2 * ypsz * NW; e += AD_NT) a.typ[e] = 0;
+  }
   sweep_fast<W, DMAX, RES>(a, sm, o, a.resume ? 1 : 0, nullptr, gridDim.x,
                            blockIdx.x, a.part + (size_t)blockIdx.x * 3 * d * r);
   if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
@@ -726,30 +858,37 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   const bool have0 = a.resume && __ldcg(a.kcount) > 0;
   if (have0) load_inverses<W>(a.Zs, r, RP, sm + o.Zx, sm + o.Zy);
   __syncthreads();
+  // Sweep it reads the reduced shares S_it (sweep 0: a.SX, a.SY from the
+  // setup; then tag it + 1, buffer it % 3) and, on the U side, Yt_it (tag
+  // it, buffer it & 1, published by the lead in sweep it - 1); it writes
+  // its shares P_it (tag it + 1, buffer it & 1), its slice of S_it+1 and,
+  // on the lead, Yt_it+1.  A U-side CTA's reading of Yt_it ends before the
+  // lead writes Yt_it+2: the lead waits for S_it+1, made from P_it.
   for (int it = 0; it < a.iters; ++it) {
     uint64_t t0 = pr ? globaltimer_ns() : 0;
-    // U-side CTAs read this sweep's Yt^T from the V side
-    small_fast<W, DMAX, RMAX>(
-        a, sm, o, have0 || it > 0, prof ? tsub : nullptr, nullptr, nullptr,
-        false, uside,
-        (a.Gu > 0 && (int)blockIdx.x == lead)
-            ? a.Ypub + (size_t)((it + 1) & 1) * ypsz : nullptr,
-        (uside && it > 0) ? a.Ypub + (size_t)(it & 1) * ypsz : nullptr);
+    SweepIO io;
+    io.sxy = it > 0 ? a.tsxy + (size_t)(it % 3) * cw : nullptr;
+    io.stag = (uint32_t)it + 1;
+    io.yin = (uside && it > 0) ? a.typ + (size_t)(it & 1) * ypsz * NW : nullptr;
+    io.ytag = (uint32_t)it;
+    io.yout = (a.Gu > 0 && (int)blockIdx.x == lead)
+                  ? a.typ + (size_t)((it + 1) & 1) * ypsz * NW : nullptr;
+    io.yotag = (uint32_t)it + 1;
+    if (!small_fast<W, DMAX, RMAX>(a, sm, o, have0 || it > 0,
+                                   prof ? tsub : nullptr, nullptr, nullptr,
+                                   false, uside, &io))
+      return;
     uint64_t t1 = pr ? globaltimer_ns() : 0;
-    sweep_fast<W, DMAX, RES>(a, sm, o, 2, prof ? tsub + 6 : nullptr,
-                             gridDim.x, blockIdx.x,
-                             a.part + (size_t)blockIdx.x * 3 * d * r);
+    sweep_fast<W, DMAX, RES>(
+        a, sm, o, 2, prof ? tsub + 6 : nullptr, gridDim.x, blockIdx.x, nullptr,
+        a.tpart + ((size_t)(it & 1) * gridDim.x + blockIdx.x) * cw,
+        (uint32_t)it + 1);
     uint64_t t2 = pr ? globaltimer_ns() : 0;
-    if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
-    uint64_t t3 = pr ? globaltimer_ns() : 0;
-    reduce_fast<W>(a, 0);
-    uint64_t t4 = pr ? globaltimer_ns() : 0;
-    if (!grid_barrier(a.bar, a.status, a.timeout_ns)) return;
+    if (!reduce_tagged<W>(a, it)) return;
     if (pr) {
-      uint64_t t5 = globaltimer_ns();
+      uint64_t t3 = globaltimer_ns();
       tw += t1 - t0; tr += t2 - t1; tb += t3 - t2;
       tph[0] += t1 - t0; tph[1] += t2 - t1; tph[2] += t3 - t2;
-      tph[3] += t4 - t3; tph[4] += t5 - t4;
     }
   }
   if (RES) fast_resident_copy<W>(a, sm, o, 1);

@@ -72,6 +72,13 @@ struct AdmmArgs {
   // first V-side CTA publishes in Ypub (two buffers, by sweep parity).
   int Gu;
   W* Ypub;
+  // Sweep loop of the fast kernel: tagged words (payload + sweep tag, see
+  // tag_put) in place of grid barriers: per-CTA shares (2 x G x 2 d r
+  // values, by sweep parity), the reduced SX, SY^T (3 x 2 d r, by sweep
+  // mod 3) and the published Yt^T (2 x d RP, by parity).
+  uint64_t* tpart;
+  uint64_t* tsxy;
+  uint64_t* typ;
 };
 
 struct AdmmSmem {
@@ -393,6 +400,18 @@ inline size_t state_bytes(int64_t m, int64_t n, int r, int d, size_t e) {
          ((2 * (size_t)r * r * e + 7) & ~size_t(7));
 }
 
+// Tagged-word counts of the fast kernel's sweep loop (sizeof(W) / 4 words
+// per value).
+inline size_t tag_part_words(int r, int d, size_t e, int G) {
+  return (size_t)2 * G * 2 * d * r * (e / 4);
+}
+inline size_t tag_sxy_words(int r, int d, size_t e) {
+  return (size_t)3 * 2 * d * r * (e / 4);
+}
+inline size_t tag_y_words(int r, int d, size_t e) {
+  return (size_t)2 * d * ((r + 3) & ~3) * (e / 4);
+}
+
 inline size_t factor_ws(int r, int d, size_t e, int G) {
   Carve cv(nullptr, SIZE_MAX);
   cv.take<char>((size_t)d * r * e);
@@ -400,6 +419,9 @@ inline size_t factor_ws(int r, int d, size_t e, int G) {
   cv.take<char>((size_t)G * 3 * d * r * e);
   cv.take<unsigned>(64);
   cv.take<char>((size_t)2 * d * ((r + 3) & ~3) * e);   // Ypub
+  cv.take<uint64_t>(tag_part_words(r, d, e, G));
+  cv.take<uint64_t>(tag_sxy_words(r, d, e));
+  cv.take<uint64_t>(tag_y_words(r, d, e));
   return cv.off;
 }
 
@@ -515,6 +537,9 @@ static cnmf_status run_factor(const void* L, const void* Rt, const void* At,
   a.part = cv.take<W>((size_t)G * 3 * d * r);
   a.bar = cv.take<unsigned>(64);
   a.Ypub = (W*)cv.take<char>((size_t)2 * d * ((r + 3) & ~3) * e);
+  a.tpart = cv.take<uint64_t>(tag_part_words(r, d, e, G));
+  a.tsxy = cv.take<uint64_t>(tag_sxy_words(r, d, e));
+  a.typ = cv.take<uint64_t>(tag_y_words(r, d, e));
   a.Gu = P.Gu;
   char* st = (char*)state;
   a.Lam = (W*)st;

@@ -169,6 +169,71 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int32_t* status,
 }
 
 // ---------------------------------------------------------------------------
+// Tagged words: a 32-bit payload and a 32-bit tag in one 64-bit word, stored
+// and loaded as single aligned 64-bit accesses (single-copy atomic), so a
+// reader that sees the tag it expects also sees the payload stored with it.
+// Producers and consumers of per-sweep data synchronise through the data
+// itself instead of a grid barrier.  A value of type W takes sizeof(W) / 4
+// words, each carrying the tag.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+template <typename W>
+__device__ __forceinline__ void tag_put(uint64_t* p, W v, uint32_t tag) {
+  const uint64_t t = (uint64_t)tag << 32;
+  if constexpr (sizeof(W) == 4) {
+    st_relaxed_u64(p, t | __float_as_uint(v));
+  } else {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    st_relaxed_u64(p, t | (b & 0xffffffffull));
+    st_relaxed_u64(p + 1, t | (b >> 32));
+  }
+}
+
+template <typename W>
+__device__ __forceinline__ W tag_value(const uint64_t* w) {
+  if constexpr (sizeof(W) == 4) {
+    return __uint_as_float((uint32_t)w[0]);
+  } else {
+    return __longlong_as_double(
+        (long long)(((w[1] & 0xffffffffull) << 32) | (w[0] & 0xffffffffull)));
+  }
+}
+
+// Re-read *p until it carries `tag` (w: the value already read).  The wait
+// is bounded like grid_barrier's: false after timeout_ns (CNMF_E_TIMEOUT,
+// abort bit raised in bar[0]) or when another CTA raised the abort bit.
+__device__ __forceinline__ bool tag_spin(const uint64_t* p, uint32_t tag,
+                                         uint64_t& w, unsigned* bar,
+                                         int32_t* status,
+                                         uint64_t timeout_ns) {
+  uint64_t t0 = 0;
+  unsigned spins = 0;
+  while ((uint32_t)(w >> 32) != tag) {
+    if ((++spins & 63u) == 0) {
+      if (ld_acquire_gpu(bar) & GRID_ABORT) return false;
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > timeout_ns) {
+        set_status(status, CNMF_E_TIMEOUT);
+        atomicOr(bar, GRID_ABORT);
+        return false;
+      }
+    }
+    w = ld_relaxed_u64(p);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Host helpers
 // ---------------------------------------------------------------------------
 struct Carve {
