@@ -436,12 +436,13 @@ struct AdmmPlan {
 // algebra after the X update, so it starts its rows earlier than a V-side
 // CTA by the second half of the chain; past a fixed start-up cost that both
 // sides pay, rows cost about 2e-5 d r us each.  Gu balances m / Gu row costs
-// against dt + n / (G - Gu) row costs.  dt = 2.8 us is the measured best on
+// against dt + n / (G - Gu) row costs.  dt = 2.3 us is the measured best on
 // GB300 at m = 20000, n = 10000, d = 30, r = 20 (the Y half itself takes
-// about 3.3 us; the V side's row sweep has a larger fixed cost).
+// about 3.3 us, but the U side also waits for the lead's Yt; the time per
+// sweep is flat within 1% for Gu from 54 to 73 there).
 inline int split_gu(int64_t m, int64_t n, int r, int d, int G) {
   if (G < 2) return 0;
-  const double c = 2e-5 * d * r, dt = 2.8;
+  const double c = 2e-5 * d * r, dt = 2.3;
   int best = 0;
   double bt = 1e300;
   for (int gu = 1; gu < G; ++gu) {
