@@ -418,10 +418,12 @@ def main(argv=None):
 
     def e2e_step(k):
         b = k % 2
-        h2d(k + 1, ev_done[1 - b])      # buffer of step k - 1, now free
         stream.wait_event(ev_in[b])
+        # the step's small inputs go to the copy engine ahead of the next
+        # step's A, which would otherwise hold them up for its whole transfer
         U.copy_(U_pin, non_blocking=True)
         Vt.copy_(Vt_pin, non_blocking=True)
+        h2d(k + 1, ev_done[1 - b])      # buffer of step k - 1, now free
         L, Rt, At, _ = cn.cnmf_compress(A_dev[b], r, d, q, SEEDS["sketch"],
                                         status=st, ws=ws_c)
         ev_done[b].record(stream)
