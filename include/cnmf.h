@@ -356,6 +356,25 @@ cnmf_status cnmf_barrier_selftest(int32_t ctas, int32_t rounds, int32_t skip,
                                   size_t ws_bytes, int32_t* dev_status,
                                   int32_t* out_rounds, cnmf_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * cnmf_tagwait_selftest: exercises the bounded waits on tagged words (a
+ * 32-bit payload and a 32-bit tag in one 64-bit word) through which
+ * cnmf_factor's register-tiled sweep loop synchronises instead of grid
+ * barriers.  A cooperative grid of `ctas` CTAs (<= SM count) runs `rounds`
+ * rounds; in round t every CTA publishes a tagged word and waits for both
+ * ring neighbours' round-t words.  If 0 <= skip < ctas, CTA `skip`
+ * publishes nothing, so its neighbours give up after timeout_ms (1..10000),
+ * write CNMF_E_TIMEOUT to *dev_status and raise the abort flag, and every
+ * CTA returns -- nothing hangs.  With skip < 0 all rounds complete and
+ * *dev_status stays 0.  *out_rounds (optional device int32) receives the
+ * number of rounds CTA 0 completed.  ws: >= 256 + 16 ctas bytes.
+ * (Library self-test; the paper has no counterpart.)
+ * ---------------------------------------------------------------------- */
+cnmf_status cnmf_tagwait_selftest(int32_t ctas, int32_t rounds, int32_t skip,
+                                  int32_t timeout_ms, void* ws,
+                                  size_t ws_bytes, int32_t* dev_status,
+                                  int32_t* out_rounds, cnmf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,9 @@ SIGNATURES = {
     "cnmf_barrier_selftest": (c_int32, [c_int32, c_int32, c_int32, c_int32,
                                         c_void_p, c_size_t, c_void_p,
                                         c_void_p, c_void_p]),
+    "cnmf_tagwait_selftest": (c_int32, [c_int32, c_int32, c_int32, c_int32,
+                                        c_void_p, c_size_t, c_void_p,
+                                        c_void_p, c_void_p]),
 }
 
 _lib = None

@@ -102,7 +102,58 @@ __global__ void k_barrier_selftest(unsigned* bar, int rounds, int skip,
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && out_rounds) *out_rounds = passed;
 }
+// Ring exchange through tagged words (the ADMM sweep loop's synchronisation):
+// in round t every CTA publishes (c + t, tag t) in buffer t & 1 and waits
+// for the round-t words of both neighbours, so no CTA gets two rounds ahead
+// of a reader of its buffer.
+__global__ void k_tagwait_selftest(unsigned* bar, uint64_t* words, int rounds,
+                                   int skip, uint64_t timeout_ns,
+                                   int32_t* status, int32_t* out_rounds) {
+  if (threadIdx.x != 0) return;
+  const int G = gridDim.x, c = blockIdx.x;
+  int passed = 0;
+  for (int t = 1; t <= rounds; ++t) {
+    if (c == skip) return;                 // this CTA never publishes
+    uint64_t* buf = words + (size_t)(t & 1) * G;
+    tag_put<float>(buf + c, (float)(c + t), (uint32_t)t);
+    bool ok = true;
+    const int nb[2] = {(c + 1) % G, (c + G - 1) % G};
+    for (int j = 0; j < 2 && ok; ++j) {
+      uint64_t w = ld_relaxed_u64(buf + nb[j]);
+      ok = tag_spin(buf + nb[j], (uint32_t)t, w, bar, status, timeout_ns);
+      if (ok && tag_value<float>(&w) != (float)(nb[j] + t)) {
+        set_status(status, CNMF_E_NONFINITE);
+        ok = false;
+      }
+    }
+    if (!ok) break;
+    ++passed;
+  }
+  if (c == 0 && out_rounds) *out_rounds = passed;
+}
 }  // namespace cnmf
+
+extern "C" cnmf_status cnmf_tagwait_selftest(int32_t ctas, int32_t rounds,
+                                             int32_t skip, int32_t timeout_ms,
+                                             void* ws, size_t ws_bytes,
+                                             int32_t* dev_status,
+                                             int32_t* out_rounds,
+                                             cnmf_stream_t stream) {
+  if (ctas < 1 || ctas > cnmf::num_sms() || rounds < 0 || timeout_ms < 1 ||
+      timeout_ms > 10000 || !ws || !dev_status ||
+      ws_bytes < 256 + 16 * (size_t)ctas)
+    return CNMF_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* bar = (unsigned*)ws;
+  uint64_t* words = (uint64_t*)((char*)ws + 256);
+  CNMF_CUDA(cudaMemsetAsync(ws, 0, 256 + 16 * (size_t)ctas, s));
+  uint64_t tns = (uint64_t)timeout_ms * 1000000ull;
+  void* args[] = {&bar, &words, &rounds, &skip, &tns, &dev_status, &out_rounds};
+  // co-resident CTAs: a cooperative launch (they wait on one another)
+  CNMF_CUDA(cudaLaunchCooperativeKernel((const void*)cnmf::k_tagwait_selftest,
+                                        dim3(ctas), dim3(32), args, 0, s));
+  return CNMF_OK;
+}
 
 extern "C" cnmf_status cnmf_barrier_selftest(int32_t ctas, int32_t rounds,
                                              int32_t skip, int32_t timeout_ms,

@@ -178,3 +178,36 @@ def test_barrier_timeout_returns_status():
     # the context is still usable
     x = torch.ones(10, device="cuda").sum()
     assert float(x) == 10.0
+
+
+def test_tagwait_timeout_returns_status():
+    torch = need_gpu()
+    import ctypes as C
+    from paper_1505_04650_gb300 import _lib
+    lib = _lib.load()
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rounds = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    ctas = min(16, nsm)
+    # every CTA publishes: 200 rounds through two buffers, status OK
+    assert lib.cnmf_tagwait_selftest(ctas, 200, -1, 1000, C.c_void_p(ws.data_ptr()),
+                                     4096, C.c_void_p(st.data_ptr()),
+                                     C.c_void_p(rounds.data_ptr()), s) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(rounds.item()) == 200
+    # CTA 3 never publishes: its neighbours give up after ~100 ms with
+    # TIMEOUT, the abort flag releases everyone else
+    import time
+    st.zero_()
+    t0 = time.time()
+    assert lib.cnmf_tagwait_selftest(ctas, 20, 3, 100, C.c_void_p(ws.data_ptr()),
+                                     4096, C.c_void_p(st.data_ptr()),
+                                     C.c_void_p(rounds.data_ptr()), s) == 0
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 5.0
+    assert int(st.item()) == 6  # CNMF_E_TIMEOUT
+    assert int(rounds.item()) < 20
+    x = torch.ones(10, device="cuda").sum()
+    assert float(x) == 10.0
