@@ -368,9 +368,10 @@ def main(argv=None):
                      "kernel": f"k_admm_fast ({iters} sweeps, one launch)",
                      "algorithmic_bytes": admm_bytes,
                      "peak_source": peaks["src"] + " (copy bandwidth)",
-                     "note": "latency-bound: two grid barriers and two r x r "
-                             "solves per sweep; the working set stays in "
-                             "shared memory and L2"},
+                     "note": "latency-bound: the small algebra (two r x r "
+                             "solves per sweep) and the waits for the "
+                             "slowest CTA's shares; the working set stays "
+                             "in shared memory and L2"},
         "roofline_sketch": {"bound": "hbm", "achieved": sketch_gbs,
                             "peak": peaks["hbm"], "unit": "GB/s",
                             "frac": sketch_gbs / peaks["hbm"],
