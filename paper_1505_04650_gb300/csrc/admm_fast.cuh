@@ -418,83 +418,106 @@ __device__ bool small_fast(const AdmmArgs<W>& a, W* sm, const FastSmem& o,
   W* H = sm + o.H;
   constexpr int KS = (DMAX * RMAX + AD_NT - 1) / AD_NT;
   constexpr int NW = sizeof(W) / 4;
-  W vy[KS];
-  if (!sxy_smem) {
-    // SX (and on U-side CTAs this sweep's Yt^T) staged in shared memory
-    // before the X Grams: all loads in flight at once, one L2 round trip.
-    // SY^T: loads issued with them, stored after the X Grams loop.
-    W vx[KS], vp[KS];
-    if (io && io->sxy) {
-      const uint64_t* sx = io->sxy;
-      const uint64_t* sy = io->sxy + (size_t)dr * NW;
-      const uint64_t* yp = io->yin;
-      const uint64_t dx = (uint64_t)io->stag << 32, dy = (uint64_t)io->ytag << 32;
-      uint64_t wx[KS][NW], wy[KS][NW], wp[KS][NW];
+  if (!sxy_smem && io && io->sxy) {
+    // Sweep loop: the reduced shares (and on U-side CTAs this sweep's
+    // Yt^T) are tagged words, all loads in flight at once.  Yt^T is needed
+    // by the X Grams loop and is waited for first; the Grams products then
+    // run while the shares may still be on their way, and SX is added to M
+    // afterwards (the same sum as adding it in the loop's epilogue).
+    const uint64_t* sx = io->sxy;
+    const uint64_t* sy = io->sxy + (size_t)dr * NW;
+    const uint64_t* yp = io->yin;
+    const uint64_t dx = (uint64_t)io->stag << 32, dy = (uint64_t)io->ytag << 32;
+    uint64_t wx[KS][NW], wy[KS][NW], wp[KS][NW];
 #pragma unroll
-      for (int k = 0; k < KS; ++k) {
-        const int e = threadIdx.x + k * AD_NT;
+    for (int k = 0; k < KS; ++k) {
+      const int e = threadIdx.x + k * AD_NT;
 #pragma unroll
-        for (int h = 0; h < NW; ++h) {
-          wx[k][h] = e < dr ? ld_relaxed_u64(sx + e * NW + h) : dx;
-          wy[k][h] = (!half && e < dr) ? ld_relaxed_u64(sy + e * NW + h) : dx;
-          wp[k][h] = (yp && e < d * RP) ? ld_relaxed_u64(yp + e * NW + h) : dy;
-        }
+      for (int h = 0; h < NW; ++h) {
+        wx[k][h] = e < dr ? ld_relaxed_u64(sx + e * NW + h) : dx;
+        wy[k][h] = (!half && e < dr) ? ld_relaxed_u64(sy + e * NW + h) : dx;
+        wp[k][h] = (yp && e < d * RP) ? ld_relaxed_u64(yp + e * NW + h) : dy;
       }
-      bool ok = true;
+    }
+    bool ok = true;
+    if (yp) {
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         const int e = threadIdx.x + k * AD_NT;
+        if (e < d * RP) {
 #pragma unroll
-        for (int h = 0; h < NW; ++h) {
-          if (e < dr)
-            ok = ok && tag_spin(sx + e * NW + h, io->stag, wx[k][h], a.bar,
-                                a.status, a.timeout_ns);
-          if (!half && e < dr)
-            ok = ok && tag_spin(sy + e * NW + h, io->stag, wy[k][h], a.bar,
-                                a.status, a.timeout_ns);
-          if (yp && e < d * RP)
+          for (int h = 0; h < NW; ++h)
             ok = ok && tag_spin(yp + e * NW + h, io->ytag, wp[k][h], a.bar,
                                 a.status, a.timeout_ns);
+          YtT[e] = tag_value<W>(wp[k]);
         }
-        vx[k] = tag_value<W>(wx[k]);
-        vy[k] = tag_value<W>(wy[k]);
-        vp[k] = tag_value<W>(wp[k]);
       }
       if (__syncthreads_or(!ok)) return false;
-    } else {
+    }
+    mark(0);
+    // At Yt^T (d x RP, At read along its columns from AtT);
+    // G = Yt Yt^T + lam I  (r x RP)
+    dual_mm<W>({M, AtT, 1, d, YtT, d, W(1), nullptr, 0, W(0), true},
+               {G, YtT, 1, RP, YtT, r, W(1), nullptr, 0, a.lam, true}, RP,
+               d, r);
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int e = threadIdx.x + k * AD_NT;
+      if (e < dr) {
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+          ok = ok && tag_spin(sx + e * NW + h, io->stag, wx[k][h], a.bar,
+                              a.status, a.timeout_ns);
+          if (!half)
+            ok = ok && tag_spin(sy + e * NW + h, io->stag, wy[k][h], a.bar,
+                                a.status, a.timeout_ns);
+        }
+        sm[o.sSX + e] = tag_value<W>(wx[k]);
+        if (!half) sm[o.sSY + e] = tag_value<W>(wy[k]);
+      }
+    }
+    if (__syncthreads_or(!ok)) return false;
+    // M = SX + At Yt^T
+    for (int e = threadIdx.x; e < dr; e += AD_NT)
+      M[(e / r) * RP + e % r] += sm[o.sSX + e];
+    SYp = sm + o.sSY;
+    __syncthreads();
+  } else {
+    W vy[KS];
+    if (!sxy_smem) {
+      // SX staged in shared memory before the X Grams; SY^T: loads issued
+      // with it, stored after the X Grams loop
+      W vx[KS];
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         const int e = threadIdx.x + k * AD_NT;
         vx[k] = e < dr ? __ldcg(SXp + e) : W(0);
         vy[k] = (!half && e < dr) ? __ldcg(SYp + e) : W(0);
-        vp[k] = W(0);
       }
-    }
-    const bool ysrc = io && io->yin;
 #pragma unroll
-    for (int k = 0; k < KS; ++k) {
-      const int e = threadIdx.x + k * AD_NT;
-      if (e < dr) sm[o.sSX + e] = vx[k];
-      if (ysrc && e < d * RP) YtT[e] = vp[k];
+      for (int k = 0; k < KS; ++k) {
+        const int e = threadIdx.x + k * AD_NT;
+        if (e < dr) sm[o.sSX + e] = vx[k];
+      }
+      SXp = sm + o.sSX;
+      __syncthreads();
     }
-    SXp = sm + o.sSX;
+    mark(0);
+    // M = SX + At Yt^T  (d x RP, At read along its columns from AtT);
+    // G = Yt Yt^T + lam I  (r x RP)
+    dual_mm<W>({M, AtT, 1, d, YtT, d, W(1), SXp, r, W(0), true},
+               {G, YtT, 1, RP, YtT, r, W(1), nullptr, 0, a.lam, true}, RP,
+               d, r);
+    if (!sxy_smem && !half) {
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int e = threadIdx.x + k * AD_NT;
+        if (e < dr) sm[o.sSY + e] = vy[k];
+      }
+      SYp = sm + o.sSY;
+    }
     __syncthreads();
   }
-  mark(0);
-  // M = SX + At Yt^T  (d x RP, At read along its columns from AtT);
-  // G = Yt Yt^T + lam I  (r x RP)
-  dual_mm<W>({M, AtT, 1, d, YtT, d, W(1), SXp, r, W(0), true},
-             {G, YtT, 1, RP, YtT, r, W(1), nullptr, 0, a.lam, true}, RP,
-             d, r);
-  if (!sxy_smem && !half) {
-#pragma unroll
-    for (int k = 0; k < KS; ++k) {
-      const int e = threadIdx.x + k * AD_NT;
-      if (e < dr) sm[o.sSY + e] = vy[k];
-    }
-    SYp = sm + o.sSY;
-  }
-  __syncthreads();
   mark(1);
   // Xt = M (Yt Yt^T + lam I)^-1
   const W* zx = solve_fast<W, RMAX>(Xt, M, T, d, G, Zx, E, F, H, sm + o.v,
