@@ -262,16 +262,40 @@ def main(argv=None):
                                     ws=ws_c)
     lam = cn.default_penalty(At, r)
 
-    def step():
-        L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st,
-                                        ws=ws_c)
+    # ---- the timed steps.  One step = one factorization (compression + 500
+    # ADMM sweeps).  Consecutive steps are independent problems, so they are
+    # pipelined on two streams: the compression of step k + 1 runs beside
+    # the ADMM sweeps of step k, each call's grids capped at half of the
+    # SMs (cnmf_set_thread_cta_limit).  The ADMM is latency-bound (every CTA
+    # repeats the small algebra), so half the SMs slow it far less than
+    # they speed up the compression running beside it.
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    cap = nsm // 2
+    sF = stream                          # ADMM sweeps
+    sC = torch.cuda.Stream(dev)          # compressions
+    U = U0.clone()
+    Vt = Vt0.clone()
+
+    def pipe_step(fa=None):
+        with torch.cuda.stream(sC):
+            L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"],
+                                            status=st, ws=ws_c)
+            ev = torch.cuda.Event()
+            ev.record(sC)
+        sF.wait_event(ev)
+        for t in (L, Rt, At):
+            t.record_stream(sF)
         U.copy_(U0)
         Vt.copy_(Vt0)
+        if fa is not None:
+            fa[0].record(sF)
         cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
-        return L, Rt, At
+        if fa is not None:
+            fa[1].record(sF)
 
+    cn.set_thread_cta_limit(cap)
     for _ in range(max(args.warmup, 3)):
-        step()
+        pipe_step()
     torch.cuda.synchronize()
     cn.raise_on_status(st, "bench warm-up")
 
@@ -279,17 +303,45 @@ def main(argv=None):
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fas = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     with Clocks(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
+        ev0.record(sC)
+        sF.wait_event(ev0)
+        for k in range(args.steps):
+            pipe_step(fas[k])
+        sF.wait_stream(sC)
+        ev1.record(sF)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ms = replicas.slowest_ms(ev0.elapsed_time(ev1) / args.steps, dev)
     cn.raise_on_status(st, "bench timed region")
     value = replicas.job_rate(1, ms, world)
+    # the dominant kernel's launches inside the timed region (CUDA events on
+    # the stream it runs on)
+    admm_ms_live = sum(f0.elapsed_time(f1) for f0, f1 in fas) / args.steps
+    cn.set_thread_cta_limit(0)
+
+    # the same steps one after the other on one stream, every SM per call
+    def seq_step():
+        L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"], status=st,
+                                        ws=ws_c)
+        U.copy_(U0)
+        Vt.copy_(Vt0)
+        cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
+    for _ in range(2):
+        seq_step()
+    torch.cuda.synchronize()
+    es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    es0.record(stream)
+    nseq = max(3, min(args.steps, 10))
+    for _ in range(nseq):
+        seq_step()
+    es1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = es0.elapsed_time(es1) / nseq
+    cn.raise_on_status(st, "bench sequential steps")
 
     # ---- phase breakdown (CUDA events, same stream)
     eb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -346,12 +398,15 @@ def main(argv=None):
 
     # ---- dominant kernel of the step: the compressed ADMM launch
     # (k_admm_fast, all 500 sweeps in one cooperative launch), timed by the
-    # events around cnmf_factor above.  Algorithmic bytes per sweep: L, R^T
-    # (d each) and U, Lam, V^T, Phi^T (r each, read and written) per row:
-    # 4 (m + n)(d + 4 r).
+    # events around each cnmf_factor inside the timed region (half of the
+    # SMs, beside the next step's compression).  Algorithmic bytes per
+    # sweep: L, R^T (d each) and U, Lam, V^T, Phi^T (r each, read and
+    # written) per row: 4 (m + n)(d + 4 r).
     admm_bytes = 4.0 * (m + n) * (d + 4 * r) * iters
-    admm_gbs = admm_bytes / (breakdown["factor_ms"] * 1e-3) / 1e9
+    admm_gbs = admm_bytes / (admm_ms_live * 1e-3) / 1e9
     traffic = _traffic("k_admm_fast", iters)
+    breakdown["sequential_ms_per_step"] = seq_ms
+    breakdown["pipelined_admm_ms"] = admm_ms_live
 
     out = {
         "metric": METRIC, "value": value, "unit": "factorizations/s",
@@ -361,11 +416,15 @@ def main(argv=None):
         "config": {"workload": WORKLOAD, "m": m, "n": n, "r": r, "d": d,
                    "q": q, "admm_iters": iters, "lambda": lam,
                    "l2": "inputs larger than L2 (A = 800 MB)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}",
+                   "pipelining": f"two streams: the compression of step "
+                                 f"k + 1 beside the ADMM sweeps of step k, "
+                                 f"each call capped at {cap} of {nsm} SMs"},
         "roofline": {"bound": "hbm", "achieved": admm_gbs,
                      "peak": peaks["hbm"], "unit": "GB/s",
                      "frac": admm_gbs / peaks["hbm"], "traffic": traffic,
-                     "kernel": f"k_admm_fast ({iters} sweeps, one launch)",
+                     "kernel": f"k_admm_fast ({iters} sweeps, one launch, "
+                               f"{cap} CTAs beside a compression)",
                      "algorithmic_bytes": admm_bytes,
                      "peak_source": peaks["src"] + " (copy bandwidth)",
                      "note": "latency-bound: the small algebra (two r x r "
@@ -395,11 +454,13 @@ def main(argv=None):
     }
 
     # ---- end to end through the public API with host buffers: every step
-    # copies its A, U0, V0^T from pinned host memory and reads U, V^T back.
-    # The copy of the next step's A (on a copy stream, into the other of two
-    # device buffers) starts as soon as the previous step's compression is
-    # done with that buffer, and overlaps this step's compression and ADMM
-    # sweeps.
+    # copies its A, U0, V0^T from pinned host memory and reads U, V^T back,
+    # pipelined like the timed steps (compressions on one stream, ADMM
+    # sweeps on another, each capped at half of the SMs).  The copy of the
+    # next step's A (a copy stream, into the other of two device buffers)
+    # starts as soon as the previous step's compression is done with that
+    # buffer.  The step's own U0, V0^T are queued before it: behind the
+    # 800 MB copy they would wait for its whole transfer.
     A_pin = torch.from_numpy(A_h).pin_memory()
     U_pin = torch.from_numpy(U0_h).pin_memory()
     Vt_pin = torch.from_numpy(Vt0_h).pin_memory()
@@ -419,29 +480,36 @@ def main(argv=None):
 
     def e2e_step(k):
         b = k % 2
-        stream.wait_event(ev_in[b])
-        # the step's small inputs go to the copy engine ahead of the next
-        # step's A, which would otherwise hold them up for its whole transfer
-        U.copy_(U_pin, non_blocking=True)
+        U.copy_(U_pin, non_blocking=True)          # on sF
         Vt.copy_(Vt_pin, non_blocking=True)
+        with torch.cuda.stream(sC):
+            sC.wait_event(ev_in[b])
+            L, Rt, At, _ = cn.cnmf_compress(A_dev[b], r, d, q, SEEDS["sketch"],
+                                            status=st, ws=ws_c)
+            ev_done[b].record(sC)
         h2d(k + 1, ev_done[1 - b])      # buffer of step k - 1, now free
-        L, Rt, At, _ = cn.cnmf_compress(A_dev[b], r, d, q, SEEDS["sketch"],
-                                        status=st, ws=ws_c)
-        ev_done[b].record(stream)
+        sF.wait_event(ev_done[b])
+        for t in (L, Rt, At):
+            t.record_stream(sF)
         cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
         U_out.copy_(U, non_blocking=True)
         Vt_out.copy_(Vt, non_blocking=True)
 
+    cn.set_thread_cta_limit(cap)
     h2d(0, None)
     e2e_step(0)
     torch.cuda.synchronize()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ee0.record(stream)
+    ee0.record(sF)
+    sC.wait_event(ee0)
+    cstream.wait_event(ee0)
     for k in range(1, args.steps + 1):
         e2e_step(k)
-    stream.wait_stream(cstream)        # the last copy ends inside the region
-    ee1.record(stream)
+    sF.wait_stream(sC)
+    sF.wait_stream(cstream)            # the last copy ends inside the region
+    ee1.record(sF)
     torch.cuda.synchronize()
+    cn.set_thread_cta_limit(0)
     cn.raise_on_status(st, "bench e2e")
     e2e_ms = replicas.slowest_ms(ee0.elapsed_time(ee1) / args.steps, dev)
     out["e2e"] = {"value": replicas.job_rate(1, e2e_ms, world),
@@ -451,8 +519,9 @@ def main(argv=None):
                   "d2h_bytes_per_step": int(U_out.numel() * 4 + Vt_out.numel() * 4),
                   "ms_per_step": e2e_ms,
                   "overlap": "the next step's H2D copy of A (copy stream, "
-                             "second device buffer) runs during this "
-                             "step's compression and ADMM sweeps"}
+                             "second device buffer) and the next "
+                             "compression run beside this step's ADMM "
+                             "sweeps"}
 
     # ---- time to the residual target vs plain ADMM (same GPU)
     if not args.no_ttt:

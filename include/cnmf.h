@@ -341,6 +341,24 @@ cnmf_status cnmf_residual_noalloc(const void* A, cnmf_dtype a_type, int64_t m,
                                   double* out2, cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_set_thread_cta_limit: caps the grid of every kernel that is sized
+ * per SM (the tensor-core products, CholeskyQR, the cooperative ADMM
+ * launch, ...) for the calls this host thread makes from now on: at most
+ * `ctas` CTAs, so each such kernel occupies at most `ctas` SMs (one CTA per
+ * SM).  0 restores the device's SM count.  Two independent calls on two
+ * streams, each capped at half the SMs, then run side by side -- e.g. the
+ * compression of one problem beside the latency-bound ADMM sweeps of
+ * another.  Workspace queries made under a cap return the capped sizes;
+ * a workspace sized without a cap fits every cap.  Results depend on the
+ * cap only through the summation order of cross-CTA sums (within the
+ * documented tolerances).  A cooperative ADMM launch below about 70 CTAs
+ * may no longer keep its rows in shared memory at large m + n (slower, not
+ * wrong).  Returns CNMF_E_INVALID_ARG for ctas < 0.
+ * (Library utility; the paper has no counterpart.)
+ * ---------------------------------------------------------------------- */
+cnmf_status cnmf_set_thread_cta_limit(int32_t ctas);
+
+/* ------------------------------------------------------------------------
  * cnmf_barrier_selftest: exercises the bounded grid barrier that the
  * persistent kernels (cnmf_factor) use.  A cooperative grid of `ctas` CTAs
  * (<= SM count) passes `rounds` barriers.  If 0 <= skip < ctas, CTA `skip`

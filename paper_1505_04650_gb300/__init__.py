@@ -26,6 +26,7 @@ __all__ = [
     "cnmf_sketch_pass", "cnmf_orth", "cnmf_compress", "cnmf_factor",
     "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
     "sketch_size", "default_penalty", "BatchProblem", "cnmf_factor_batched",
+    "set_thread_cta_limit",
 ]
 
 
@@ -102,6 +103,12 @@ def default_penalty(Atilde: torch.Tensor, r: int) -> float:
     """lambda = phi = ||Atilde||_F / r (the balanced reading of Alg. 4's
     unspecified penalties; a host-side scalar from the compressed matrix)."""
     return float(torch.linalg.norm(Atilde.double())) / r
+
+
+def set_thread_cta_limit(ctas: int):
+    """Cap the per-SM grids of this host thread's later calls at `ctas` CTAs
+    (0: the whole device), so two calls on two streams can share the SMs."""
+    _check(lib().cnmf_set_thread_cta_limit(int(ctas)), "cnmf_set_thread_cta_limit")
 
 
 # --------------------------------------------------------------------------

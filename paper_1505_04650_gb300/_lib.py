@@ -100,6 +100,7 @@ SIGNATURES = {
     "cnmf_tagwait_selftest": (c_int32, [c_int32, c_int32, c_int32, c_int32,
                                         c_void_p, c_size_t, c_void_p,
                                         c_void_p, c_void_p]),
+    "cnmf_set_thread_cta_limit": (c_int32, [c_int32]),
 }
 
 _lib = None

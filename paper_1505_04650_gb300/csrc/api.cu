@@ -6,6 +6,14 @@
 
 namespace cnmf {
 
+// Largest grid (CTAs) of the persistent and per-SM-sized kernels launched
+// from this host thread (0: the device's SM count); see
+// cnmf_set_thread_cta_limit.
+static thread_local int t_cta_limit = 0;
+
+// SM count of the current device, or the calling thread's CTA limit when
+// that is smaller.  Every grid that is sized per SM comes from here, so the
+// limit bounds the SMs one call occupies.
 int num_sms() {
   static int cached[64] = {0};
   int dev = 0;
@@ -20,7 +28,8 @@ int num_sms() {
       (void)cudaGetLastError();
     cached[dev] = v > 0 ? v : 1;
   }
-  return cached[dev];
+  const int full = cached[dev];
+  return (t_cta_limit > 0 && t_cta_limit < full) ? t_cta_limit : full;
 }
 
 int max_smem_optin() {
@@ -171,5 +180,11 @@ extern "C" cnmf_status cnmf_barrier_selftest(int32_t ctas, int32_t rounds,
   void* args[] = {&bar, &rounds, &skip, &tns, &dev_status, &out_rounds};
   CNMF_CUDA(cudaLaunchCooperativeKernel((const void*)cnmf::k_barrier_selftest,
                                         dim3(ctas), dim3(128), args, 0, s));
+  return CNMF_OK;
+}
+
+extern "C" cnmf_status cnmf_set_thread_cta_limit(int32_t ctas) {
+  if (ctas < 0) return CNMF_E_INVALID_ARG;
+  cnmf::t_cta_limit = ctas;
   return CNMF_OK;
 }

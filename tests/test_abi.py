@@ -92,3 +92,8 @@ def test_workspace_queries(lib):
     assert lib.snmf_select_workspace(100, 80, 10, 2) > 0
     assert lib.cnmf_plain_state_bytes(100, 80, 5, 0) == \
         (2 * 100 * 5 + 2 * 80 * 5) * 8 + 8
+
+
+def test_thread_cta_limit_rejects_negative(lib):
+    assert lib.cnmf_set_thread_cta_limit(-1) == 1   # CNMF_E_INVALID_ARG
+    assert lib.cnmf_set_thread_cta_limit(0) == 0

@@ -256,3 +256,45 @@ def test_snmf_anchors_match_oracle(storage, m, n, r, d, q):
     print(f"min SPA margin {margins.min():.2e}")
     # Rhat^T is basis-dependent only through Q, which is unique
     assert rel(to_np(rh), Rhat.T) <= (1e-10 if storage == "f64" else 1e-4)
+
+
+@pytest.mark.parametrize("limit", [7, "half"])
+def test_cta_limit_two_streams_match_oracle(limit):
+    """cnmf_set_thread_cta_limit: a compression on one stream beside the
+    ADMM sweeps of another problem on a second stream, each grid capped,
+    both still match the oracle (compression: signal projector 1e-5;
+    ADMM: U, V after 20 sweeps 1e-4)."""
+    torch = need_gpu()
+    import paper_1505_04650_gb300 as cn
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    cap = nsm // 2 if limit == "half" else limit
+    m, n, r, d = 2000, 1500, 10, 20
+    A32 = synth.as_storage(synth.lowrank(m, n, r, 0.01, 1001), "f32")
+    A = A32.astype(np.float64)
+    Af, L, Rt, At, U0, V0 = _factor_case(3000, 2000, 20, 30, 4, 0.01, 1000, "f32")
+    lam = np.linalg.norm(At) / 20
+    dev = lambda x: torch.tensor(x, dtype=torch.float32).cuda()
+    Ad = to_dev(A32, "f32")
+    Ld_in, Rtd_in, Atd_in = dev(L), dev(Rt), dev(At)
+    Ud, Vtd = dev(U0), dev(V0.T.copy())
+    sA, sB = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    try:
+        cn.set_thread_cta_limit(cap)
+        with torch.cuda.stream(sA):
+            Ud, Vtd, state, stf = cn.cnmf_factor(Ld_in, Rtd_in, Atd_in, Ud, Vtd,
+                                                 lam, lam, 20)
+        with torch.cuda.stream(sB):
+            Ld, Rtd, Atd, stc = cn.cnmf_compress(Ad, r, d, 4, seed=2001)
+        torch.cuda.synchronize()
+    finally:
+        cn.set_thread_cta_limit(0)
+    assert int(stf.item()) == 0 and int(stc.item()) == 0
+    Om, Ps = ophil.test_matrices(2001, m, n, d)
+    L0, Rt0, _, _ = ocomp.compress(A, Om, Ps, 4)
+    assert rel(_signal_projector(to_np(Ld), A, r), _signal_projector(L0, A, r)) <= 1e-5
+    assert rel(_signal_projector(to_np(Rtd), A.T, r),
+               _signal_projector(Rt0, A.T, r)) <= 1e-5
+    ref = oadmm.admm(L, Rt, At, U0, V0, lam=lam, phi=lam, iters=20)
+    eu, ev = rel(to_np(Ud), ref.U), rel(to_np(Vtd).T, ref.V)
+    assert eu <= 1e-4 and ev <= 1e-4
