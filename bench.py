@@ -218,6 +218,9 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the served-stream measurement")
     ap.add_argument("--serving-requests", type=int, default=4096)
+    ap.add_argument("--admm-ctas", type=int, default=0,
+                    help="SMs for the ADMM stream of the pipelined steps "
+                         "(the compression stream gets the rest; 0: half)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the wide-SNMF and mixed-precision lines")
     args = ap.parse_args(argv)
@@ -265,18 +268,20 @@ def main(argv=None):
     # ---- the timed steps.  One step = one factorization (compression + 500
     # ADMM sweeps).  Consecutive steps are independent problems, so they are
     # pipelined on two streams: the compression of step k + 1 runs beside
-    # the ADMM sweeps of step k, each call's grids capped at half of the
-    # SMs (cnmf_set_thread_cta_limit).  The ADMM is latency-bound (every CTA
+    # the ADMM sweeps of step k, each call's grids capped at its share of
+    # the SMs (cnmf_set_thread_cta_limit; --admm-ctas, default half).  The ADMM is latency-bound (every CTA
     # repeats the small algebra), so half the SMs slow it far less than
     # they speed up the compression running beside it.
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    cap = nsm // 2
+    cap = args.admm_ctas if 0 < args.admm_ctas < nsm else nsm // 2
+    cap_c = nsm - cap                    # the compression stream's SMs
     sF = stream                          # ADMM sweeps
     sC = torch.cuda.Stream(dev)          # compressions
     U = U0.clone()
     Vt = Vt0.clone()
 
     def pipe_step(fa=None):
+        cn.set_thread_cta_limit(cap_c)
         with torch.cuda.stream(sC):
             L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"],
                                             status=st, ws=ws_c)
@@ -287,13 +292,13 @@ def main(argv=None):
             t.record_stream(sF)
         U.copy_(U0)
         Vt.copy_(Vt0)
+        cn.set_thread_cta_limit(cap)
         if fa is not None:
             fa[0].record(sF)
         cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
         if fa is not None:
             fa[1].record(sF)
 
-    cn.set_thread_cta_limit(cap)
     for _ in range(max(args.warmup, 3)):
         pipe_step()
     torch.cuda.synchronize()
@@ -418,8 +423,8 @@ def main(argv=None):
                    "l2": "inputs larger than L2 (A = 800 MB)",
                    "parallelism": f"replicas{world}",
                    "pipelining": f"two streams: the compression of step "
-                                 f"k + 1 beside the ADMM sweeps of step k, "
-                                 f"each call capped at {cap} of {nsm} SMs"},
+                                 f"k + 1 ({cap_c} SMs) beside the ADMM "
+                                 f"sweeps of step k ({cap} of {nsm} SMs)"},
         "roofline": {"bound": "hbm", "achieved": admm_gbs,
                      "peak": peaks["hbm"], "unit": "GB/s",
                      "frac": admm_gbs / peaks["hbm"], "traffic": traffic,
@@ -482,6 +487,7 @@ def main(argv=None):
         b = k % 2
         U.copy_(U_pin, non_blocking=True)          # on sF
         Vt.copy_(Vt_pin, non_blocking=True)
+        cn.set_thread_cta_limit(cap_c)
         with torch.cuda.stream(sC):
             sC.wait_event(ev_in[b])
             L, Rt, At, _ = cn.cnmf_compress(A_dev[b], r, d, q, SEEDS["sketch"],
@@ -491,11 +497,11 @@ def main(argv=None):
         sF.wait_event(ev_done[b])
         for t in (L, Rt, At):
             t.record_stream(sF)
+        cn.set_thread_cta_limit(cap)
         cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
         U_out.copy_(U, non_blocking=True)
         Vt_out.copy_(Vt, non_blocking=True)
 
-    cn.set_thread_cta_limit(cap)
     h2d(0, None)
     e2e_step(0)
     torch.cuda.synchronize()
