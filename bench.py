@@ -178,9 +178,10 @@ def launches_per_step(q, chunks_gt1=True):
 # from one ncu capture of the kernel as it stands, with the SHA-256 of the
 # sources it was compiled from; None once those sources change.
 TRAFFIC = {
-    # profiles/k_admm_fast_m20000_n10000_r20_d30.md: 8.564 MB read +
-    # 0.035 MB written by the 500-sweep launch
-    "k_admm_fast": {"bytes_per_unit": 8.598272e6 / 500, "sha": "f84d7106d33918e2"},
+    # profiles/k_admm_fast_m20000_n10000_r20_d30.md: 8.850 MB read +
+    # 0.076 MB written by the 500-sweep launch (76 CTAs, as in the
+    # pipelined steps)
+    "k_admm_fast": {"bytes_per_unit": 8.925696e6 / 500, "sha": "5530797371ffa88d"},
     # profiles/k_tc_prod_f32_m20000_n10000_d30.md: A X 805.23 + 2.25 MB,
     # A^T Y 868.03 + 4.13 MB; one unit = one pass (both products)
     "k_tc_prod": {"bytes_per_unit": 1679.634432e6, "sha": "d74ba8dadf2e3d3d"},
