@@ -836,7 +836,8 @@ __global__ void __launch_bounds__(AD_NT) k_admm_fast(AdmmArgs<W> a) {
   const bool prof = a.phase_ns && (int)blockIdx.x == lead && threadIdx.x == 0;
   const bool profu = a.phase_ns && a.Gu > 0 && blockIdx.x == 0 &&
                      threadIdx.x == 0 && a.phase_ns_len >= 20;
-  // with room for it, every CTA's time before and in the first barrier
+  // with room for it, every CTA's time in the small algebra, the row sweep
+  // and the reduction
   const bool profc = a.phase_ns && threadIdx.x == 0 &&
                      a.phase_ns_len >= 20 + 3 * (int)gridDim.x;
   const bool pr = prof || profu || profc;

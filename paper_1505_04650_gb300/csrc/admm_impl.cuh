@@ -12,9 +12,11 @@
 // (U and V use the old multipliers, as printed) and accumulates its share
 // of the NEXT sweep's SX = L^T (lam U - Lam) and SY = (phi V - Phi) R^T from
 // the rows it just wrote.  The shares are summed over CTAs in CTA order
-// (CTA c sums slice c of the entries), with two bounded grid barriers per
-// sweep.  The small algebra runs in the working precision: the r x r
-// systems are SPD and well scaled by lam, phi > 0.
+// (CTA c sums slice c of the entries): the generic kernel here with two
+// bounded grid barriers per sweep, the register-tiled kernel (admm_fast.cuh)
+// through tagged words without grid barriers.  The small algebra runs in
+// the working precision: the r x r systems are SPD and well scaled by
+// lam, phi > 0.
 #include <algorithm>
 #include <mutex>
 
