@@ -181,7 +181,7 @@ TRAFFIC = {
     # profiles/k_admm_fast_m20000_n10000_r20_d30.md: 8.850 MB read +
     # 0.076 MB written by the 500-sweep launch (76 CTAs, as in the
     # pipelined steps)
-    "k_admm_fast": {"bytes_per_unit": 8.925696e6 / 500, "sha": "5530797371ffa88d"},
+    "k_admm_fast": {"bytes_per_unit": 8.925696e6 / 500, "sha": "d661a8aa8d42cdeb"},
     # profiles/k_tc_prod_f32_m20000_n10000_d30.md: A X 805.23 + 2.25 MB,
     # A^T Y 868.03 + 4.13 MB; one unit = one pass (both products)
     "k_tc_prod": {"bytes_per_unit": 1679.634432e6, "sha": "d74ba8dadf2e3d3d"},
