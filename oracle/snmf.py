@@ -1,4 +1,5 @@
-"""Compressed separable NMF column selection (Alg. 3, steps 1-2) with SPA.
+"""Compressed separable NMF (Alg. 3): column selection with SPA (steps 1-2)
+and the right factor (step 3).
 
 TEST INFRASTRUCTURE -- only tests, the smoke check and the benchmark's
 CPU-baseline leg call this.  FP64 NumPy.
@@ -13,7 +14,14 @@ spell it out; this is its standard greedy form:
         u  = Rhat[:, j*] / ||Rhat[:, j*]||
         Rhat <- (I - u u^T) Rhat
 The column norms are recomputed from the explicitly projected matrix at
-every step.  K is returned in selection order, together with the per-step
+every step.
+
+Step 3 solves, for every column i, the nonnegative least-squares problem
+    Y[:, i] = argmin_{h >= 0} ||Rhat[:, i] - Rhat[:, K] h||_2
+(h has r entries, one per selected column; the printed h in R^{r + r_ov}
+reads as a slip, since Rhat[:, K] has r columns).  ``right_factor`` calls
+SciPy's Lawson-Hanson NNLS per column, a library routine used as one step;
+when Rhat[:, K] has full column rank the minimiser is unique.  K is returned in selection order, together with the per-step
 margin mu_k = (N1 - N2) / N1 over the two largest squared norms, which
 tells a test whether the selection is decided with room to spare.
 """
@@ -50,3 +58,16 @@ def snmf_select(A: np.ndarray, Omega: np.ndarray, r: int, q: int):
     Q, Rhat = snmf_basis(A, Omega, q)
     K, margins = spa(Rhat, r)
     return K, margins, Q, Rhat
+
+
+def right_factor(Rhat: np.ndarray, K) -> np.ndarray:
+    """Alg. 3 step 3: Y (r x n), column i the NNLS fit of Rhat[:, i] by the
+    selected columns Rhat[:, K] (FP64, SciPy's Lawson-Hanson per column)."""
+    from scipy.optimize import nnls
+    R = np.asarray(Rhat, dtype=np.float64)
+    B = R[:, np.asarray(K, dtype=np.int64)]
+    n = R.shape[1]
+    Y = np.empty((B.shape[1], n))
+    for i in range(n):
+        Y[:, i], _ = nnls(B, R[:, i])
+    return Y

@@ -62,3 +62,72 @@ def test_noisy_separable_with_margin():
     K, margins, Q, Rhat = snmf.snmf_select(A, Om, 10, 2)
     assert sorted(K) == sorted(anchors)
     assert margins.min() > 1e-4
+
+
+# ---- Alg. 3 step 3: the right factor (per-column NNLS)
+
+def _kkt(B, b, h):
+    """Largest violation of the NNLS optimality conditions at h: h >= 0,
+    gradient g = B^T (B h - b) >= 0 where h = 0 and = 0 where h > 0."""
+    g = B.T @ (B @ h - b)
+    scale = np.linalg.norm(B.T @ b) + 1e-300
+    viol = np.where(h > 0, np.abs(g), np.maximum(-g, 0.0))
+    return max(viol.max() / scale, max(-h.min(), 0.0))
+
+
+def test_right_factor_kkt_random():
+    g = np.random.default_rng(7)
+    for d, n, r in [(12, 40, 4), (30, 25, 9), (5, 8, 1)]:
+        R = g.standard_normal((d, n))
+        K = g.choice(n, r, replace=False)
+        Y = snmf.right_factor(R, K)
+        assert Y.shape == (r, n)
+        for i in range(n):
+            assert _kkt(R[:, K], R[:, i], Y[:, i]) <= 1e-10
+
+
+def test_right_factor_exact_on_separable():
+    # noiseless separable Rhat = W [I | H] Pi with H >= 0: the selected
+    # columns reproduce every column with the planted weights
+    g = np.random.default_rng(3)
+    d, r, n = 10, 4, 30
+    Wb = g.random((d, r))
+    H = g.random((r, n - r))
+    M = np.concatenate([np.eye(r), H], axis=1)
+    perm = g.permutation(n)
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    R = Wb @ M[:, inv]
+    K = perm[:r]
+    Y = snmf.right_factor(R, K)
+    assert np.abs(Y - M[:, inv]).max() <= 1e-10
+    # a selected column is its own unit vector
+    for j, k in enumerate(K):
+        assert np.abs(Y[:, k] - np.eye(r)[:, j]).max() <= 1e-12
+
+
+def test_right_factor_brute_force_tiny():
+    # enumerate every passive set of a 3-column problem: the minimiser is
+    # the feasible unconstrained fit on some passive set with the smallest
+    # residual
+    import itertools
+    g = np.random.default_rng(11)
+    d, r = 6, 3
+    for _ in range(20):
+        B = g.standard_normal((d, r))
+        b = g.standard_normal(d)
+        best, hbest = np.inf, None
+        for mask in itertools.product([0, 1], repeat=r):
+            P = [j for j in range(r) if mask[j]]
+            h = np.zeros(r)
+            if P:
+                sol, *_ = np.linalg.lstsq(B[:, P], b, rcond=None)
+                if sol.min() < 0:
+                    continue
+                h[P] = sol
+            res = np.linalg.norm(B @ h - b)
+            if res < best - 1e-14:
+                best, hbest = res, h
+        R = np.concatenate([B, b[:, None]], axis=1)
+        Y = snmf.right_factor(R, np.arange(r))
+        assert np.abs(Y[:, r] - hbest).max() <= 1e-10
