@@ -302,6 +302,39 @@ cnmf_status snmf_select(const void* A, cnmf_dtype a_type, int64_t m,
                         cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * snmf_right_factor: compressed separable NMF, Alg. 3 step 3 (Sec. IV):
+ * for every column i of Rhat (d x n),
+ *   Y[:, i] = argmin_{h >= 0} || Rhat[:, i] - Rhat[:, K] h ||_2 ,
+ * the nonnegative least-squares fit by the r selected columns.  The paper
+ * leaves the NNLS solver open; this one is projected cyclic coordinate
+ * descent on the shared Gram matrix G = Rhat[:, K]^T Rhat[:, K] (one column
+ * per thread), started from the unconstrained minimiser G^-1 b with its
+ * negative entries set to zero, run until the projected gradient is at
+ * most tol times
+ * max_j |(Rhat[:, K]^T Rhat[:, i])_j| or for max_sweeps sweeps; when
+ * Rhat[:, K] has full column rank the minimiser is unique and the sweeps
+ * converge to it.
+ *   Rhat_t   n x d (pitch ld >= d), = Rhat^T as snmf_select writes it;
+ *            w_type CNMF_F64 or CNMF_F32 (arithmetic in w_type).
+ *   anchors  device, r int64 column indices (snmf_select's); an index
+ *            outside [0, n) sets CNMF_E_INVALID_ARG in *dev_status.
+ *   Y        out, r x n (pitch ldy >= n), w_type.
+ *   unconverged  optional device int32, incremented once per column that
+ *            did not reach the tolerance within max_sweeps (the caller
+ *            zeroes it).
+ *   1 <= r <= min(d, 64), d <= 128, max_sweeps >= 1, tol >= 0.
+ * ---------------------------------------------------------------------- */
+size_t snmf_right_factor_workspace(int64_t n, int32_t d, int32_t r,
+                                   cnmf_dtype w_type);
+cnmf_status snmf_right_factor(const void* Rhat_t, cnmf_dtype w_type,
+                              int64_t n, int32_t d, int64_t ld,
+                              const int64_t* anchors, int32_t r,
+                              int32_t max_sweeps, double tol, void* Y,
+                              int64_t ldy, int32_t* unconverged, void* ws,
+                              size_t ws_bytes, int32_t* dev_status,
+                              cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_residual: out2[0] = ||A - U V||_F^2, out2[1] = ||A||_F^2 (FP64,
  * device), in one read of A (Sec. V reports sqrt(out2[0] / out2[1])).
  *   U m x r, Vt n x r in w_type (CNMF_F64 or CNMF_F32), 1 <= r <= 128.

@@ -26,7 +26,7 @@ __all__ = [
     "cnmf_sketch_pass", "cnmf_orth", "cnmf_compress", "cnmf_factor",
     "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
     "sketch_size", "default_penalty", "BatchProblem", "cnmf_factor_batched",
-    "set_thread_cta_limit",
+    "set_thread_cta_limit", "snmf_right_factor",
 ]
 
 
@@ -324,6 +324,31 @@ def snmf_select(A: torch.Tensor, r: int, d: int, q: int, seed: int,
                           _ptr(Omega), _ptr(anchors), _ptr(rh), _ptr(ws),
                           ws.numel(), _ptr(st), _stream(dev)), "snmf_select")
     return (anchors, rh, st) if return_rhat else (anchors, st)
+
+
+def snmf_right_factor(Rhat_t: torch.Tensor, anchors: torch.Tensor,
+                      max_sweeps: int = 1000, tol: float = 1e-6,
+                      status: torch.Tensor | None = None, ws=None):
+    """Alg. 3 step 3 -> (Y r x n, unconverged int32[1], status): the
+    nonnegative least-squares fit of every column of Rhat by the columns
+    `anchors` (Rhat_t n x d as snmf_select returns it)."""
+    n, d = Rhat_t.shape
+    w = Rhat_t.dtype
+    _dense(Rhat_t, (n, d), w, "Rhat_t")
+    r = anchors.numel()
+    dev = Rhat_t.device
+    Y = torch.empty(r, n, dtype=w, device=dev)
+    unconv = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = status if status is not None else _status(dev)
+    lb = lib()
+    nb = lb.snmf_right_factor_workspace(n, d, r, _DT[w])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(lb.snmf_right_factor(_ptr(Rhat_t), _DT[w], n, d, d, _ptr(anchors),
+                                r, max_sweeps, tol, _ptr(Y), n, _ptr(unconv),
+                                _ptr(ws), ws.numel(), _ptr(st), _stream(dev)),
+           "snmf_right_factor")
+    return Y, unconv, st
 
 
 def cnmf_residual(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,

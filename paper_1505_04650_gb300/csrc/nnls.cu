@@ -1,0 +1,323 @@
+// Right factor of compressed separable NMF (Alg. 3 step 3; Sec. IV): for
+// every column i of Rhat (d x n),
+//   Y[:, i] = argmin_{h >= 0} || Rhat[:, i] - Rhat[:, K] h ||_2 .
+// All n problems share the matrix B = Rhat[:, K] (d x r), so they share its
+// Gram matrix G = B^T B (r x r); only b_i = B^T Rhat[:, i] differs.  The
+// paper leaves the NNLS solver open; this one is projected cyclic
+// coordinate descent on 1/2 h^T G h - b^T h, one column per thread:
+//   h_j <- max(0, h_j - g_j / G_jj),  g <- g + (h_j,new - h_j,old) G[:, j]
+// with g = G h - b (recomputed exactly every 16 sweeps, so rounding does not
+// drift), until the projected gradient max_j (h_j > 0 ? |g_j| : max(-g_j, 0))
+// is at most tol * max_j |b_j|, or max_sweeps.  Each step is the exact
+// minimiser along one coordinate of a strictly convex quadratic (G SPD when
+// B has full column rank), so the iterates converge to the unique minimiser.
+//
+// The sweeps start from the unconstrained minimiser G^-1 b with its negative
+// entries set to zero: when it has none (most columns of a near-separable
+// matrix) it is the answer, and otherwise a close start.
+//
+// Launches: (1) one CTA gathers B from the rows K of Rhat^T and forms G and
+// G^-1 (Gauss-Jordan in FP64);
+// (2) the library's product kernel forms Bt = Rhat^T B (n x r, = b_i^T by
+// rows); (3) k_nnls: 128 columns per CTA, b staged through shared memory
+// for coalesced loads, Y written by rows (coalesced over columns).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cnmf {
+
+constexpr int NN_NT = 128;
+
+// B (d x r, pitch rp) = rows K of Rt (n x d) transposed; G (r x r, pitch
+// rp) = B^T B in W arithmetic; gd[j] = 1 / G_jj (0 for a zero column);
+// Gi (r x r, pitch rp) = G^-1 by Gauss-Jordan in FP64 (no pivoting: G is
+// SPD when B has full column rank; a zero pivot leaves its row at zero, and
+// the solver then starts from whatever finite point that gives).
+template <typename W>
+constexpr size_t nnls_setup_smem(int d, int rp, int r) {
+  return (((size_t)d * rp * sizeof(W) + 15) & ~size_t(15)) +
+         (size_t)r * 2 * r * sizeof(double) + (size_t)r * sizeof(double);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256)
+    k_nnls_setup(const W* __restrict__ Rt, int64_t n, int d, int64_t ld,
+                 const int64_t* __restrict__ K, int r, int rp,
+                 W* __restrict__ B, W* __restrict__ G, W* __restrict__ gd,
+                 W* __restrict__ Gi, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* Bs = reinterpret_cast<W*>(smem_raw);   // d x rp
+  double* J = reinterpret_cast<double*>(
+      smem_raw + (((size_t)d * rp * sizeof(W) + 15) & ~size_t(15)));  // r x 2r
+  double* fac = J + (size_t)r * 2 * r;                                 // r
+  __shared__ double pk_s;
+  __shared__ int bad_s;
+  if (threadIdx.x == 0) bad_s = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < d * r; e += blockDim.x) {
+    const int k = e / r, j = e % r;
+    const int64_t kj = K[j];
+    W v = W(0);
+    if (kj < 0 || kj >= n) bad_s = 1;
+    else v = Rt[kj * ld + k];
+    Bs[k * rp + j] = v;
+    B[k * rp + j] = v;
+  }
+  __syncthreads();
+  if (bad_s) {
+    if (threadIdx.x == 0) set_status(status, CNMF_E_INVALID_ARG);
+    return;
+  }
+  const int r2 = 2 * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int a = e / r, c = e % r;
+    W s = W(0);
+    for (int k = 0; k < d; ++k) s = fma(Bs[k * rp + a], Bs[k * rp + c], s);
+    G[a * rp + c] = s;
+    J[a * r2 + c] = (double)s;
+    J[a * r2 + r + c] = a == c ? 1.0 : 0.0;
+    if (a == c) gd[a] = s > W(0) ? W(1) / s : W(0);
+  }
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      const double p = J[k * r2 + k];
+      pk_s = p > 0.0 ? 1.0 / p : 0.0;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < r2; c += blockDim.x) J[k * r2 + c] *= pk_s;
+    for (int a = threadIdx.x; a < r; a += blockDim.x)
+      if (a != k) fac[a] = J[a * r2 + k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r2; e += blockDim.x) {
+      const int a = e / r2, c = e % r2;
+      if (a != k) J[e] = fma(-fac[a], J[k * r2 + c], J[e]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int a = e / r, c = e % r;
+    Gi[a * rp + c] = (W)J[a * r2 + r + c];
+  }
+}
+
+// One column per thread.  Bt (n x r, pitch r) holds b_i by rows; Y (r x n,
+// pitch ldy).  G, 1/diag(G) and the tile's b rows are staged in shared
+// memory (dynamic: nnls_smem bytes); the column-j slice of G that a step
+// needs is the same for every lane (broadcast).
+template <typename W, int RMAX>
+constexpr size_t nnls_smem() {
+  return ((size_t)2 * RMAX * RMAX + RMAX + (size_t)NN_NT * (RMAX + 1)) *
+         sizeof(W);
+}
+
+template <typename W, int RMAX>
+__global__ void __launch_bounds__(NN_NT)
+    k_nnls(const W* __restrict__ Bt, int64_t n, int r, int rp,
+           const W* __restrict__ G, const W* __restrict__ gd,
+           const W* __restrict__ Gi, int max_sweeps, W tol,
+           W* __restrict__ Y, int64_t ldy, int32_t* __restrict__ unconverged) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* Gs = reinterpret_cast<W*>(smem_raw);       // RMAX x RMAX
+  W* Gis = Gs + RMAX * RMAX;                     // RMAX x RMAX
+  W* gds = Gis + RMAX * RMAX;                    // RMAX
+  W* bts = gds + RMAX;                           // NN_NT x (RMAX + 1)
+  for (int e = threadIdx.x; e < RMAX * RMAX; e += NN_NT) {
+    const int a = e / RMAX, c = e % RMAX;
+    Gs[e] = (a < r && c < r) ? G[a * rp + c] : W(0);
+    Gis[e] = (a < r && c < r) ? Gi[a * rp + c] : W(0);
+  }
+  for (int e = threadIdx.x; e < RMAX; e += NN_NT) gds[e] = e < r ? gd[e] : W(0);
+  for (int64_t t0 = (int64_t)blockIdx.x * NN_NT; t0 < n;
+       t0 += (int64_t)gridDim.x * NN_NT) {
+    const int64_t cnt = min((int64_t)NN_NT, n - t0);
+    __syncthreads();
+    // this tile's b rows: cnt x r contiguous values, coalesced; padding 0
+    for (int64_t e = threadIdx.x; e < (int64_t)NN_NT * RMAX; e += NN_NT) {
+      const int64_t i = e / RMAX;
+      const int j = (int)(e % RMAX);
+      bts[i * (RMAX + 1) + j] =
+          (i < cnt && j < r) ? Bt[(t0 + i) * r + j] : W(0);
+    }
+    __syncthreads();
+    const W* b = bts + threadIdx.x * (RMAX + 1);   // this column's b
+    const int64_t col = t0 + threadIdx.x;
+    const bool have = threadIdx.x < cnt;
+    W h[RMAX], g[RMAX];
+    W bmax = W(0);
+    // start: the unconstrained minimiser G^-1 b with its negative entries
+    // set to zero -- already the answer when it has none (most columns of a
+    // near-separable matrix), else a close starting point
+#pragma unroll
+    for (int a = 0; a < RMAX; ++a) {
+      W sacc = W(0);
+#pragma unroll
+      for (int c = 0; c < RMAX; ++c) sacc = fma(Gis[a * RMAX + c], b[c], sacc);
+      h[a] = sacc > W(0) ? sacc : W(0);   // NaN -> 0
+      const W ab = fabs(b[a]);
+      bmax = ab > bmax ? ab : bmax;
+    }
+    const W lim = tol * bmax;
+    bool conv = false;
+    // sweep sw: exact gradient g = G h - b every 16 sweeps (no drift), the
+    // stopping test, then one cyclic pass over the coordinates
+    for (int sw = 0; sw <= max_sweeps; ++sw) {
+      if ((sw & 15) == 0) {
+#pragma unroll
+        for (int a = 0; a < RMAX; ++a) {
+          W sacc = -b[a];
+#pragma unroll
+          for (int c = 0; c < RMAX; ++c) sacc = fma(Gs[a * RMAX + c], h[c], sacc);
+          g[a] = sacc;
+        }
+      }
+      W pg = W(0);
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        const W v = h[j] > W(0) ? fabs(g[j]) : (g[j] < W(0) ? -g[j] : W(0));
+        pg = v > pg ? v : pg;
+      }
+      conv = !(pg > lim);   // NaN never counts as converged
+      // the warp runs until every lane is done (lanes past n count as done)
+      if (__all_sync(0xffffffffu, conv || !have) || sw == max_sweeps) break;
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        if (j < r) {
+          W hn = h[j] - g[j] * gds[j];
+          hn = hn > W(0) ? hn : W(0);
+          const W dl = hn - h[j];
+          h[j] = hn;
+          const W* gc = Gs + j * RMAX;   // G symmetric: row j = column j
+#pragma unroll
+          for (int a = 0; a < RMAX; ++a) g[a] = fma(dl, gc[a], g[a]);
+        }
+      }
+    }
+    if (have) {
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j)
+        if (j < r) Y[(int64_t)j * ldy + col] = h[j];
+      if (!conv && unconverged) atomicAdd(unconverged, 1);
+    }
+  }
+}
+
+template <typename W, int RMAX>
+static cnmf_status nnls_launch(int grid, const W* Bt, int64_t n, int r,
+                               int rp, const W* G, const W* gd, const W* Gi,
+                               int max_sweeps, W tol, W* Y, int64_t ldy,
+                               int32_t* unconverged, cudaStream_t s) {
+  constexpr size_t smem = nnls_smem<W, RMAX>();
+  if (cudaFuncSetAttribute((const void*)k_nnls<W, RMAX>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return CNMF_E_CUDA;
+  k_nnls<W, RMAX><<<grid, NN_NT, smem, s>>>(Bt, n, r, rp, G, gd, Gi,
+                                            max_sweeps, tol, Y, ldy,
+                                            unconverged);
+  CNMF_CUDA(cudaGetLastError());
+  return CNMF_OK;
+}
+
+struct NnlsLayout {
+  void* B;
+  void* G;
+  void* gd;
+  void* Gi;
+  void* bt;
+  void* prod_ws;
+  size_t prod_bytes;
+  size_t bytes;
+};
+
+static NnlsLayout nnls_layout(void* ws, int64_t n, int d, int r,
+                              cnmf_dtype w) {
+  Carve cv(ws, SIZE_MAX);
+  NnlsLayout L;
+  const size_t e = wbytes(w);
+  const int rp = r;
+  L.B = cv.take<char>((size_t)d * rp * e);
+  L.G = cv.take<char>((size_t)r * rp * e);
+  L.gd = cv.take<char>((size_t)r * e);
+  L.Gi = cv.take<char>((size_t)r * rp * e);
+  L.bt = cv.take<char>((size_t)n * r * e);
+  L.prod_bytes = prod_workspace(n, d, r, w);
+  L.prod_ws = cv.take<char>(L.prod_bytes);
+  L.bytes = cv.off;
+  return L;
+}
+
+template <typename W>
+static cnmf_status nnls_run(const void* Rt, int64_t n, int d, int64_t ld,
+                            const int64_t* K, int r, int max_sweeps,
+                            double tol, void* Y, int64_t ldy,
+                            int32_t* unconverged, const NnlsLayout& L,
+                            int32_t* status, cudaStream_t s) {
+  const int rp = r;
+  // dynamic shared memory plus the kernel's static words may pass the
+  // default 48 KiB: always raise the limit to what this launch needs
+  const size_t smem = nnls_setup_smem<W>(d, rp, r);
+  if (cudaFuncSetAttribute((const void*)k_nnls_setup<W>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return CNMF_E_CUDA;
+  k_nnls_setup<W><<<1, 256, smem, s>>>((const W*)Rt, n, d, ld, K, r, rp,
+                                       (W*)L.B, (W*)L.G, (W*)L.gd, (W*)L.Gi,
+                                       status);
+  CNMF_CUDA(cudaGetLastError());
+  // b_i for every column: Bt = Rhat^T B (n x r)
+  const cnmf_dtype w = sizeof(W) == 8 ? CNMF_F64 : CNMF_F32;
+  ProdArgs p{Rt, w, n, d, ld, false, L.B, rp, r, L.bt, r, r, status};
+  CNMF_TRY(launch_prod(p, L.prod_ws, L.prod_bytes, s));
+  const int64_t tiles = (n + NN_NT - 1) / NN_NT;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 8 * num_sms()));
+  const W t = (W)tol;
+  if (r <= 16)
+    return nnls_launch<W, 16>(grid, (const W*)L.bt, n, r, rp, (const W*)L.G,
+                              (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, (W*)Y, ldy,
+                              unconverged, s);
+  if (r <= 32)
+    return nnls_launch<W, 32>(grid, (const W*)L.bt, n, r, rp, (const W*)L.G,
+                              (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, (W*)Y, ldy,
+                              unconverged, s);
+  return nnls_launch<W, 64>(grid, (const W*)L.bt, n, r, rp, (const W*)L.G,
+                            (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, (W*)Y, ldy,
+                            unconverged, s);
+  return CNMF_OK;
+}
+
+}  // namespace cnmf
+
+using namespace cnmf;
+
+extern "C" size_t snmf_right_factor_workspace(int64_t n, int32_t d, int32_t r,
+                                              cnmf_dtype w_type) {
+  if (n < 1 || d < 1 || d > 128 || r < 1 || r > 64 || r > d ||
+      (w_type != CNMF_F64 && w_type != CNMF_F32))
+    return 0;
+  return nnls_layout(nullptr, n, d, r, w_type).bytes;
+}
+
+extern "C" cnmf_status snmf_right_factor(const void* Rhat_t, cnmf_dtype w_type,
+                                         int64_t n, int32_t d, int64_t ld,
+                                         const int64_t* anchors, int32_t r,
+                                         int32_t max_sweeps, double tol,
+                                         void* Y, int64_t ldy,
+                                         int32_t* unconverged, void* ws,
+                                         size_t ws_bytes, int32_t* dev_status,
+                                         cnmf_stream_t stream) {
+  if ((w_type != CNMF_F64 && w_type != CNMF_F32) || !Rhat_t || !anchors ||
+      !Y || !ws || n < 1 || d < 1 || d > 128 || ld < d || r < 1 || r > 64 ||
+      r > d || ldy < n || max_sweeps < 1 || !(tol >= 0.0))
+    return CNMF_E_INVALID_ARG;
+  NnlsLayout L = nnls_layout(ws, n, d, r, w_type);
+  if (ws_bytes < L.bytes) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (w_type == CNMF_F64)
+    return nnls_run<double>(Rhat_t, n, d, ld, anchors, r, max_sweeps, tol, Y,
+                            ldy, unconverged, L, dev_status, s);
+  return nnls_run<float>(Rhat_t, n, d, ld, anchors, r, max_sweeps, tol, Y,
+                         ldy, unconverged, L, dev_status, s);
+}

@@ -97,3 +97,24 @@ def test_workspace_queries(lib):
 def test_thread_cta_limit_rejects_negative(lib):
     assert lib.cnmf_set_thread_cta_limit(-1) == 1   # CNMF_E_INVALID_ARG
     assert lib.cnmf_set_thread_cta_limit(0) == 0
+
+
+def test_right_factor_invalid_arguments(lib):
+    E = 1
+    fake = C.c_void_p(16)
+    ok = dict(n=100, d=10, ld=10, r=4, sweeps=10, tol=1e-6, ldy=100)
+    def call(**kw):
+        a = dict(ok, **kw)
+        return lib.snmf_right_factor(fake, 1, a["n"], a["d"], a["ld"], fake,
+                                     a["r"], a["sweeps"], a["tol"], fake,
+                                     a["ldy"], None, fake, 1 << 30, None, None)
+    assert call(r=11) == E           # r > d
+    assert call(r=65, d=70, ld=70) == E
+    assert call(sweeps=0) == E
+    assert call(tol=-1.0) == E
+    assert call(ld=9) == E
+    assert call(ldy=99) == E
+    assert call(d=129, ld=129) == E
+    assert lib.snmf_right_factor(None, 1, 100, 10, 10, fake, 4, 10, 1e-6, fake,
+                                 100, None, fake, 1 << 30, None, None) == E
+    assert lib.snmf_right_factor_workspace(100, 10, 11, 1) == 0
