@@ -181,6 +181,24 @@ cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type, int64_t m,
                           cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_compress_gaussian: the Gaussian-compression baseline the paper
+ * compares against (Sec. II, note on data-agnostic compression: Q =
+ * s^-1/2 Omega), applied on both sides with s = d and no power iteration or
+ * orthonormalisation:
+ *   L = d^-1/2 Psi (m x d, Philox stream 1),  R^T = d^-1/2 Omega (n x d,
+ *   stream 0) -- the test matrices cnmf_compress draws for the same seed --
+ *   then A-tilde = L^T A R^T (d x d) as in cnmf_compress.
+ * Arguments as cnmf_compress (same workspace query), without r, q, Omega
+ * and Psi; L and Rt are dense (pitch d), in the working type.
+ * ---------------------------------------------------------------------- */
+cnmf_status cnmf_compress_gaussian(const void* A, cnmf_dtype a_type,
+                                   int64_t m, int64_t n, int64_t lda,
+                                   int32_t d, uint64_t seed, void* L,
+                                   void* Rt, void* Atilde, void* ws,
+                                   size_t ws_bytes, int32_t* dev_status,
+                                   cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_factor: `p->iters` sweeps of compressed ADMM (Alg. 4, App. B):
  *   Xt <- (Atilde Yt^T + lam L^T U - L^T Lam)(Yt Yt^T + lam I)^-1
  *   Yt <- (Xt^T Xt + phi I)^-1 (Xt^T Atilde + phi V R^T - Phi R^T)

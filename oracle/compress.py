@@ -16,6 +16,12 @@ Sec. III applies Alg. 1 to A and to A^T to get L (m x d, orthonormal
 columns) and R (d x n, orthonormal rows); the library stores R^T (n x d).
 Sec. III defines A-check = A R^T and App. B (Alg. 4, setup) the compressed
 matrix A-tilde = L^T A R^T.
+
+Gaussian compression (Sec. II, the note on data-agnostic compression) is
+the baseline the paper compares against: Q = s^-1/2 Omega with a Gaussian
+Omega of s columns and no power iteration or orthonormalisation.
+``compress_gaussian`` applies it on both sides with s = d: L = d^-1/2 Psi,
+R^T = d^-1/2 Omega, then A-check and A-tilde as above.
 """
 from __future__ import annotations
 
@@ -77,3 +83,15 @@ def snmf_basis(A: np.ndarray, Omega: np.ndarray, q: int):
     A = np.asarray(A, dtype=np.float64)
     Q = sketch_left(A, Omega, q)
     return Q, Q.T @ A
+
+
+def compress_gaussian(A: np.ndarray, Omega: np.ndarray, Psi: np.ndarray):
+    """Two-sided Gaussian compression (Sec. II note): L = d^-1/2 Psi (m x d),
+    R^T = d^-1/2 Omega (n x d).  Returns (L, Rt, Acheck, Atilde)."""
+    A = np.asarray(A, dtype=np.float64)
+    d = Omega.shape[1]
+    c = 1.0 / np.sqrt(d)
+    L = np.asarray(Psi, dtype=np.float64) * c
+    Rt = np.asarray(Omega, dtype=np.float64) * c
+    Acheck = A @ Rt
+    return L, Rt, Acheck, L.T @ Acheck

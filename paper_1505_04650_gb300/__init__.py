@@ -26,7 +26,7 @@ __all__ = [
     "cnmf_sketch_pass", "cnmf_orth", "cnmf_compress", "cnmf_factor",
     "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
     "sketch_size", "default_penalty", "BatchProblem", "cnmf_factor_batched",
-    "set_thread_cta_limit", "snmf_right_factor",
+    "set_thread_cta_limit", "snmf_right_factor", "cnmf_compress_gaussian",
 ]
 
 
@@ -191,6 +191,28 @@ def cnmf_compress(A: torch.Tensor, r: int, d: int, q: int, seed: int,
                            _ptr(Omega), _ptr(Psi), _ptr(Lm), _ptr(Rt),
                            _ptr(At), _ptr(ws), ws.numel(), _ptr(st),
                            _stream(dev)), "cnmf_compress")
+    return Lm, Rt, At, st
+
+
+def cnmf_compress_gaussian(A: torch.Tensor, d: int, seed: int,
+                           status: torch.Tensor | None = None, ws=None):
+    """Gaussian-compression baseline -> (L m x d, Rt n x d, Atilde, status):
+    L = d^-1/2 Psi, R^T = d^-1/2 Omega (no power iteration or QR)."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    dev = A.device
+    Lm = torch.empty(m, d, dtype=w, device=dev)
+    Rt = torch.empty(n, d, dtype=w, device=dev)
+    At = torch.empty(d, d, dtype=w, device=dev)
+    st = status if status is not None else _status(dev)
+    L = lib()
+    nb = L.cnmf_compress_workspace(m, n, d, _DT[A.dtype])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(L.cnmf_compress_gaussian(_ptr(A), _DT[A.dtype], m, n, lda, d, seed,
+                                    _ptr(Lm), _ptr(Rt), _ptr(At), _ptr(ws),
+                                    ws.numel(), _ptr(st), _stream(dev)),
+           "cnmf_compress_gaussian")
     return Lm, Rt, At, st
 
 

@@ -83,6 +83,10 @@ SIGNATURES = {
                               c_int32, c_int32, c_int32, c_uint64, c_void_p,
                               c_void_p, c_void_p, c_void_p, c_size_t,
                               c_void_p, c_void_p]),
+    "cnmf_compress_gaussian": (c_int32, [c_void_p, c_int32, c_int64, c_int64,
+                                         c_int64, c_int32, c_uint64, c_void_p,
+                                         c_void_p, c_void_p, c_void_p,
+                                         c_size_t, c_void_p, c_void_p]),
     "snmf_right_factor_workspace": (c_size_t, [c_int64, c_int32, c_int32,
                                                c_int32]),
     "snmf_right_factor": (c_int32, [c_void_p, c_int32, c_int64, c_int32,

@@ -10,6 +10,7 @@
 // is L and the n x d panel is R^T.  One more product
 // gives A-check = A R^T and then A-tilde = L^T A-check (Alg. 4 setup).
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -21,6 +22,26 @@ static bool valid_type(cnmf_dtype t) {
 }
 static cnmf_dtype work_type(cnmf_dtype a) {
   return a == CNMF_F64 ? CNMF_F64 : CNMF_F32;
+}
+
+// x[0 .. count) *= c
+template <typename W>
+__global__ void k_scale(W* __restrict__ x, int64_t count, W c) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= c;
+}
+
+static cnmf_status launch_scale(void* x, int64_t count, cnmf_dtype w,
+                                double c, cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((count + 255) / 256, 4 * num_sms()));
+  if (w == CNMF_F64)
+    k_scale<double><<<grid, 256, 0, s>>>((double*)x, count, c);
+  else
+    k_scale<float><<<grid, 256, 0, s>>>((float*)x, count, (float)c);
+  CNMF_CUDA(cudaGetLastError());
+  return CNMF_OK;
 }
 
 struct CompressLayout {
@@ -165,6 +186,38 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
     X = zn; ldx = KP;
     Y = zm; ldy = KP;
   }
+  // A-check = A R^T (m x d), then A-tilde = L^T A-check (d x d)
+  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, KP, d, dev_status};
+  CNMF_TRY(launch_prod(pc, lay.prod_ws, lay.prod_bytes, s));
+  CNMF_TRY(launch_cross(L, d, lay.acheck, KP, m, d, w, Atilde, d, lay.orth_ws,
+                        lay.orth_bytes, s));
+  return CNMF_OK;
+}
+
+extern "C" cnmf_status cnmf_compress_gaussian(const void* A, cnmf_dtype a_type,
+                                              int64_t m, int64_t n,
+                                              int64_t lda, int32_t d,
+                                              uint64_t seed, void* L, void* Rt,
+                                              void* Atilde, void* ws,
+                                              size_t ws_bytes,
+                                              int32_t* dev_status,
+                                              cnmf_stream_t stream) {
+  if (!valid_type(a_type) || !A || !L || !Rt || !Atilde || !ws || m < 1 ||
+      n < 1 || lda < n || d < 1 || d > 128 || d > m || d > n)
+    return CNMF_E_INVALID_ARG;
+  CompressLayout lay = compress_layout(ws, m, n, d, a_type);
+  if (ws_bytes < lay.bytes) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cnmf_dtype w = work_type(a_type);
+  const int KP = lay.KP;
+  // L = d^-1/2 Psi (stream 1, m x d), R^T = d^-1/2 Omega (stream 0, n x d):
+  // the test matrices of cnmf_compress, without power iteration or
+  // orthonormalisation
+  const double c = 1.0 / std::sqrt((double)d);
+  CNMF_TRY(launch_gaussian(seed, 1, m * (int64_t)d, w, L, s));
+  CNMF_TRY(launch_scale(L, m * (int64_t)d, w, c, s));
+  CNMF_TRY(launch_gaussian(seed, 0, n * (int64_t)d, w, Rt, s));
+  CNMF_TRY(launch_scale(Rt, n * (int64_t)d, w, c, s));
   // A-check = A R^T (m x d), then A-tilde = L^T A-check (d x d)
   ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, KP, d, dev_status};
   CNMF_TRY(launch_prod(pc, lay.prod_ws, lay.prod_bytes, s));

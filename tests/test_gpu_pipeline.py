@@ -298,3 +298,28 @@ def test_cta_limit_two_streams_match_oracle(limit):
     ref = oadmm.admm(L, Rt, At, U0, V0, lam=lam, phi=lam, iters=20)
     eu, ev = rel(to_np(Ud), ref.U), rel(to_np(Vtd).T, ref.V)
     assert eu <= 1e-4 and ev <= 1e-4
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_compress_gaussian_matches_oracle(storage):
+    """The Gaussian-compression baseline: L, R^T are the scaled Philox test
+    matrices (elementwise, the Gaussian's own rounding plus one product),
+    A-tilde = L^T A R^T within a componentwise bound on |L|^T |A| |R^T|
+    (FP64: 1e-12; FP32 / BF16 storage with FP32 work: 1e-4)."""
+    torch = need_gpu()
+    import paper_1505_04650_gb300 as cn
+    m, n, d = 300, 257, 12
+    As = synth.as_storage(synth.lowrank(m, n, 5, 0.01, 77), storage)
+    Aw = synth.widen(As, storage)
+    Ld, Rtd, Atd, st = cn.cnmf_compress_gaussian(to_dev(As, storage), d, seed=123)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    Om, Ps = ophil.test_matrices(123, m, n, d)
+    L0, Rt0, _, At0 = ocomp.compress_gaussian(Aw, Om, Ps)
+    L, Rt, At = to_np(Ld), to_np(Rtd), to_np(Atd)
+    u = 2.0 ** -53 if storage == "f64" else 2.0 ** -24
+    assert np.abs(L - L0).max() <= 8 * u * np.abs(L0).max()
+    assert np.abs(Rt - Rt0).max() <= 8 * u * np.abs(Rt0).max()
+    bound = np.abs(L0).T @ np.abs(Aw) @ np.abs(Rt0)
+    tol = 1e-12 if storage == "f64" else 1e-4
+    assert np.all(np.abs(At - At0) <= tol * bound)

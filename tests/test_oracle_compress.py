@@ -3,7 +3,9 @@
 P1 orthonormality; P2 Eckart-Young lower bound; P3 Theorem 1 expectation
 bound (w = 0) and agreement of the re-orthonormalised power scheme with the
 literal B = (A A^T)^w A Omega; P4 exact range capture for rank-r A with
-d = r; orth() against the uniqueness of the thin QR factor.
+d = r; orth() against the uniqueness of the thin QR factor.  Gaussian
+compression (the paper's baseline): norm preservation on average and the
+operand order of A-tilde on a one-entry A.
 """
 import numpy as np
 import pytest
@@ -108,3 +110,34 @@ def test_power_iterations_drive_error_to_optimum():
          for w in (0, 2, 6)]
     assert e[2] <= e[1] * 1.0001 and e[1] <= e[0] * 1.0001
     assert e[2] <= sig[5] * 1.05
+
+
+# ---- Gaussian compression baseline (Sec. II note)
+
+def test_gaussian_compression_preserves_norms_on_average():
+    # E ||L^T x||^2 = ||x||^2 for L = d^-1/2 (i.i.d. N(0, 1)) (m x d): the
+    # scaling that makes the Gaussian projection norm-preserving.  Over 400
+    # draws the mean ratio is within 4 standard errors of 1 (one draw has
+    # variance 2 / d).
+    from oracle import philox
+    m, n, d = 60, 7, 8
+    x = np.random.default_rng(1).standard_normal(m)
+    ratios = []
+    for seed in range(400):
+        Om, Ps = philox.test_matrices(seed, m, n, d)
+        L, _, _, _ = compress.compress_gaussian(np.zeros((m, n)), Om, Ps)
+        ratios.append(np.sum((L.T @ x) ** 2) / np.sum(x ** 2))
+    se = np.sqrt(2.0 / d) / np.sqrt(len(ratios))
+    assert abs(np.mean(ratios) - 1.0) <= 4 * se
+
+
+def test_gaussian_compression_operand_order():
+    # A = e_i e_j^T picks row i of L and row j of R^T: A-tilde = L[i]^T Rt[j]
+    from oracle import philox
+    m, n, d = 9, 6, 3
+    Om, Ps = philox.test_matrices(5, m, n, d)
+    A = np.zeros((m, n))
+    A[4, 2] = 1.0
+    L, Rt, Ach, At = compress.compress_gaussian(A, Om, Ps)
+    assert np.allclose(At, np.outer(L[4], Rt[2]), rtol=0, atol=1e-15)
+    assert np.allclose(Ach[4], Rt[2], rtol=0, atol=1e-15)
