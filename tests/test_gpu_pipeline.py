@@ -5,7 +5,7 @@ cnmf_factor_plain (Alg. 4 with L = I, R = I) and snmf_select (Alg. 3 steps
 1-2).  Both sides get the same inputs: the GPU reads the storage-form A, the
 oracle its FP64 widening; test matrices come from the same Philox stream;
 factor tests feed both sides the oracle's (L, Rt, Atilde) in the working
-precision.  Acceptance (spec tolerances, readings in the design doc):
+precision.  Acceptance (the tolerances the readings of the paper fix):
 projector 1e-5 (FP32, planted well-conditioned input and the rank-r signal
 projector) / 1e-10 (FP64); U, V after 20 sweeps 1e-4 (FP32) / 1e-10
 (FP64); final objective 1e-3; SNMF anchors bit-exact as a set.
