@@ -151,7 +151,10 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1000.0 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "config": {"workload": WORKLOAD, "m": CFG["m"], "n": CFG["n"],
+                   "r": CFG["r"], "d": CFG["d"], "q": CFG["q"],
+                   "admm_iters": CFG["iters"],
+                   "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": value, "unit": "factorizations/s",
                          "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "factorizations/s",
