@@ -353,6 +353,31 @@ cnmf_status snmf_right_factor(const void* Rhat_t, cnmf_dtype w_type,
                               cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_factor_als: compressed alternating NMF (Alg. 2, Sec. III) with exact
+ * nonnegative least-squares steps (the paper admits any NNLS method; this
+ * is the solver of snmf_right_factor).  With A-check = A R^T (m x d) and
+ * A-hat = L^T A (d x n), `iters` times:
+ *   Y-check = Y R^T;  X[i] = argmin_{x >= 0} ||A-check[i] - x Y-check||
+ *   X-hat = L^T X;    Y[:, j] = argmin_{y >= 0} ||A-hat[:, j] - X-hat y||
+ *   A  m x n (pitch lda) in a_type; L (m x d), Rt (n x d, = R^T) dense, in
+ *      the working type (CNMF_F64 for F64 A, else CNMF_F32).
+ *   X  out, m x r;  Y  in/out, r x n (the start Y0 on entry), working type.
+ *   max_sweeps, tol  the NNLS stopping rule of snmf_right_factor, per step.
+ *   unconverged  optional device int32, incremented per row or column that
+ *      stopped on max_sweeps (over all steps; the caller zeroes it).
+ *   1 <= r <= min(d, 64), d <= min(128, m, n), iters >= 0.
+ * ---------------------------------------------------------------------- */
+size_t cnmf_factor_als_workspace(int64_t m, int64_t n, int32_t r, int32_t d,
+                                 cnmf_dtype a_type);
+cnmf_status cnmf_factor_als(const void* A, cnmf_dtype a_type, int64_t m,
+                            int64_t n, int64_t lda, const void* L,
+                            const void* Rt, int32_t r, int32_t d,
+                            int32_t iters, int32_t max_sweeps, double tol,
+                            void* X, void* Y, int32_t* unconverged, void* ws,
+                            size_t ws_bytes, int32_t* dev_status,
+                            cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_residual: out2[0] = ||A - U V||_F^2, out2[1] = ||A||_F^2 (FP64,
  * device), in one read of A (Sec. V reports sqrt(out2[0] / out2[1])).
  *   U m x r, Vt n x r in w_type (CNMF_F64 or CNMF_F32), 1 <= r <= 128.

@@ -27,6 +27,7 @@ __all__ = [
     "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
     "sketch_size", "default_penalty", "BatchProblem", "cnmf_factor_batched",
     "set_thread_cta_limit", "snmf_right_factor", "cnmf_compress_gaussian",
+    "cnmf_factor_als",
 ]
 
 
@@ -371,6 +372,35 @@ def snmf_right_factor(Rhat_t: torch.Tensor, anchors: torch.Tensor,
                                 _ptr(ws), ws.numel(), _ptr(st), _stream(dev)),
            "snmf_right_factor")
     return Y, unconv, st
+
+
+def cnmf_factor_als(A: torch.Tensor, L: torch.Tensor, Rt: torch.Tensor,
+                    Y0: torch.Tensor, iters: int, max_sweeps: int = 1000,
+                    tol: float = 1e-6, status: torch.Tensor | None = None,
+                    ws=None):
+    """Alg. 2 with exact NNLS steps -> (X m x r, Y r x n, unconverged,
+    status); Y0 (r x n) is the start (copied, not modified)."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    d = L.shape[1]
+    r = Y0.shape[0]
+    _dense(L, (m, d), w, "L")
+    _dense(Rt, (n, d), w, "Rt")
+    _dense(Y0, (r, n), w, "Y0")
+    dev = A.device
+    X = torch.empty(m, r, dtype=w, device=dev)
+    Y = Y0.clone()
+    unconv = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = status if status is not None else _status(dev)
+    lb = lib()
+    nb = lb.cnmf_factor_als_workspace(m, n, r, d, _DT[A.dtype])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(lb.cnmf_factor_als(_ptr(A), _DT[A.dtype], m, n, lda, _ptr(L),
+                              _ptr(Rt), r, d, iters, max_sweeps, tol, _ptr(X),
+                              _ptr(Y), _ptr(unconv), _ptr(ws), ws.numel(),
+                              _ptr(st), _stream(dev)), "cnmf_factor_als")
+    return X, Y, unconv, st
 
 
 def cnmf_residual(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,

@@ -16,6 +16,12 @@
 // entries set to zero: when it has none (most columns of a near-separable
 // matrix) it is the answer, and otherwise a close start.
 //
+// The same batched solver runs both steps of compressed alternating NMF
+// with exact nonnegative least-squares steps (Alg. 2, Sec. III; the paper
+// allows any NNLS method): the X step solves, for every row of A-check,
+// against Y-check^T, and the Y step, for every column of A-hat, against
+// X-hat.
+//
 // Launches: (1) one CTA gathers B from the rows K of Rhat^T and forms G and
 // G^-1 (Gauss-Jordan in FP64);
 // (2) the library's product kernel forms Bt = Rhat^T B (n x r, = b_i^T by
@@ -41,12 +47,15 @@ constexpr size_t nnls_setup_smem(int d, int rp, int r) {
          (size_t)r * 2 * r * sizeof(double) + (size_t)r * sizeof(double);
 }
 
+// B comes either from the rows K of Rt (K non-null) or from Bsrc with
+// B[k][j] = Bsrc[k sk + j sj].
 template <typename W>
 __global__ void __launch_bounds__(256)
     k_nnls_setup(const W* __restrict__ Rt, int64_t n, int d, int64_t ld,
-                 const int64_t* __restrict__ K, int r, int rp,
-                 W* __restrict__ B, W* __restrict__ G, W* __restrict__ gd,
-                 W* __restrict__ Gi, int32_t* status) {
+                 const int64_t* __restrict__ K, const W* __restrict__ Bsrc,
+                 int64_t sk, int64_t sj, int r, int rp, W* __restrict__ B,
+                 W* __restrict__ G, W* __restrict__ gd, W* __restrict__ Gi,
+                 int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* Bs = reinterpret_cast<W*>(smem_raw);   // d x rp
   double* J = reinterpret_cast<double*>(
@@ -58,10 +67,14 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   for (int e = threadIdx.x; e < d * r; e += blockDim.x) {
     const int k = e / r, j = e % r;
-    const int64_t kj = K[j];
     W v = W(0);
-    if (kj < 0 || kj >= n) bad_s = 1;
-    else v = Rt[kj * ld + k];
+    if (K) {
+      const int64_t kj = K[j];
+      if (kj < 0 || kj >= n) bad_s = 1;
+      else v = Rt[kj * ld + k];
+    } else {
+      v = Bsrc[k * sk + j * sj];
+    }
     Bs[k * rp + j] = v;
     B[k * rp + j] = v;
   }
@@ -103,8 +116,8 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// One column per thread.  Bt (n x r, pitch r) holds b_i by rows; Y (r x n,
-// pitch ldy).  G, 1/diag(G) and the tile's b rows are staged in shared
+// One column per thread.  Bt (n x r, pitch r) holds b_i by rows; solution
+// i, entry j goes to Y[j ysj + i ysc].  G, 1/diag(G) and the tile's b rows are staged in shared
 // memory (dynamic: nnls_smem bytes); the column-j slice of G that a step
 // needs is the same for every lane (broadcast).
 template <typename W, int RMAX>
@@ -118,7 +131,8 @@ __global__ void __launch_bounds__(NN_NT)
     k_nnls(const W* __restrict__ Bt, int64_t n, int r, int rp,
            const W* __restrict__ G, const W* __restrict__ gd,
            const W* __restrict__ Gi, int max_sweeps, W tol,
-           W* __restrict__ Y, int64_t ldy, int32_t* __restrict__ unconverged) {
+           W* __restrict__ Y, int64_t ysj, int64_t ysc,
+           int32_t* __restrict__ unconverged) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* Gs = reinterpret_cast<W*>(smem_raw);       // RMAX x RMAX
   W* Gis = Gs + RMAX * RMAX;                     // RMAX x RMAX
@@ -198,7 +212,7 @@ __global__ void __launch_bounds__(NN_NT)
     if (have) {
 #pragma unroll
       for (int j = 0; j < RMAX; ++j)
-        if (j < r) Y[(int64_t)j * ldy + col] = h[j];
+        if (j < r) Y[(int64_t)j * ysj + col * ysc] = h[j];
       if (!conv && unconverged) atomicAdd(unconverged, 1);
     }
   }
@@ -207,15 +221,16 @@ __global__ void __launch_bounds__(NN_NT)
 template <typename W, int RMAX>
 static cnmf_status nnls_launch(int grid, const W* Bt, int64_t n, int r,
                                int rp, const W* G, const W* gd, const W* Gi,
-                               int max_sweeps, W tol, W* Y, int64_t ldy,
-                               int32_t* unconverged, cudaStream_t s) {
+                               int max_sweeps, W tol, W* Y, int64_t ysj,
+                               int64_t ysc, int32_t* unconverged,
+                               cudaStream_t s) {
   constexpr size_t smem = nnls_smem<W, RMAX>();
   if (cudaFuncSetAttribute((const void*)k_nnls<W, RMAX>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return CNMF_E_CUDA;
   k_nnls<W, RMAX><<<grid, NN_NT, smem, s>>>(Bt, n, r, rp, G, gd, Gi,
-                                            max_sweeps, tol, Y, ldy,
+                                            max_sweeps, tol, Y, ysj, ysc,
                                             unconverged);
   CNMF_CUDA(cudaGetLastError());
   return CNMF_OK;
@@ -249,10 +264,16 @@ static NnlsLayout nnls_layout(void* ws, int64_t n, int d, int r,
   return L;
 }
 
+// Solves, for every row i of M (rows x d, pitch ldm), min_{h >= 0}
+// ||M[i] - h^T B^T||, B (d x r) gathered from the rows K of Rt (pitch ld)
+// or read from Bsrc with strides (sk, sj); solution i, entry j to
+// Y[j ysj + i ysc].
 template <typename W>
-static cnmf_status nnls_run(const void* Rt, int64_t n, int d, int64_t ld,
-                            const int64_t* K, int r, int max_sweeps,
-                            double tol, void* Y, int64_t ldy,
+static cnmf_status nnls_run(const W* M, int64_t ldm, int64_t rows, int d,
+                            const W* Rt, int64_t nrt, int64_t ld,
+                            const int64_t* K, const W* Bsrc, int64_t sk,
+                            int64_t sj, int r, int max_sweeps, double tol,
+                            W* Y, int64_t ysj, int64_t ysc,
                             int32_t* unconverged, const NnlsLayout& L,
                             int32_t* status, cudaStream_t s) {
   const int rp = r;
@@ -263,28 +284,96 @@ static cnmf_status nnls_run(const void* Rt, int64_t n, int d, int64_t ld,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return CNMF_E_CUDA;
-  k_nnls_setup<W><<<1, 256, smem, s>>>((const W*)Rt, n, d, ld, K, r, rp,
+  k_nnls_setup<W><<<1, 256, smem, s>>>(Rt, nrt, d, ld, K, Bsrc, sk, sj, r, rp,
                                        (W*)L.B, (W*)L.G, (W*)L.gd, (W*)L.Gi,
                                        status);
   CNMF_CUDA(cudaGetLastError());
-  // b_i for every column: Bt = Rhat^T B (n x r)
+  // right-hand sides for every row: Bt = M B (rows x r)
   const cnmf_dtype w = sizeof(W) == 8 ? CNMF_F64 : CNMF_F32;
-  ProdArgs p{Rt, w, n, d, ld, false, L.B, rp, r, L.bt, r, r, status};
+  ProdArgs p{M, w, rows, d, ldm, false, L.B, rp, r, L.bt, r, r, status};
   CNMF_TRY(launch_prod(p, L.prod_ws, L.prod_bytes, s));
-  const int64_t tiles = (n + NN_NT - 1) / NN_NT;
+  const int64_t tiles = (rows + NN_NT - 1) / NN_NT;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 8 * num_sms()));
   const W t = (W)tol;
   if (r <= 16)
-    return nnls_launch<W, 16>(grid, (const W*)L.bt, n, r, rp, (const W*)L.G,
-                              (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, (W*)Y, ldy,
-                              unconverged, s);
+    return nnls_launch<W, 16>(grid, (const W*)L.bt, rows, r, rp, (const W*)L.G,
+                              (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, Y,
+                              ysj, ysc, unconverged, s);
   if (r <= 32)
-    return nnls_launch<W, 32>(grid, (const W*)L.bt, n, r, rp, (const W*)L.G,
-                              (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, (W*)Y, ldy,
-                              unconverged, s);
-  return nnls_launch<W, 64>(grid, (const W*)L.bt, n, r, rp, (const W*)L.G,
-                            (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, (W*)Y, ldy,
-                            unconverged, s);
+    return nnls_launch<W, 32>(grid, (const W*)L.bt, rows, r, rp, (const W*)L.G,
+                              (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, Y,
+                              ysj, ysc, unconverged, s);
+  return nnls_launch<W, 64>(grid, (const W*)L.bt, rows, r, rp, (const W*)L.G,
+                            (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, Y,
+                            ysj, ysc, unconverged, s);
+}
+
+struct AlsLayout {
+  void* ach;    // A-check = A R^T, m x d
+  void* aht;    // A-hat^T = A^T L, n x d
+  void* yc;     // Y-check = Y R^T, r x d
+  void* xh;     // X-hat = L^T X, d x r
+  void* prod_ws;
+  size_t prod_bytes;
+  NnlsLayout nn;
+  size_t bytes;
+};
+
+static AlsLayout als_layout(void* ws, int64_t m, int64_t n, int r, int d,
+                            cnmf_dtype a_type) {
+  Carve cv(ws, SIZE_MAX);
+  AlsLayout L;
+  const cnmf_dtype w = a_type == CNMF_F64 ? CNMF_F64 : CNMF_F32;
+  const size_t e = wbytes(w);
+  L.ach = cv.take<char>((size_t)m * d * e);
+  L.aht = cv.take<char>((size_t)n * d * e);
+  L.yc = cv.take<char>((size_t)r * d * e);
+  L.xh = cv.take<char>((size_t)d * r * e);
+  size_t pb = prod_workspace(m, n, d, a_type);
+  pb = std::max(pb, prod_workspace(r, n, d, w));
+  pb = std::max(pb, prod_workspace(m, d, r, w));
+  L.prod_bytes = pb;
+  L.prod_ws = cv.take<char>(pb);
+  char* nb = (char*)(ws ? (char*)ws + cv.off : nullptr);
+  L.nn = nnls_layout(nb, std::max(m, n), d, r, w);
+  cv.take<char>(L.nn.bytes);
+  L.bytes = cv.off;
+  return L;
+}
+
+template <typename W>
+static cnmf_status als_run(const void* A, cnmf_dtype a_type, int64_t m,
+                           int64_t n, int64_t lda, const W* Lm, const W* Rt,
+                           int r, int d, int iters, int max_sweeps,
+                           double tol, W* X, W* Y, int32_t* unconverged,
+                           const AlsLayout& L, int32_t* status,
+                           cudaStream_t s) {
+  const cnmf_dtype w = sizeof(W) == 8 ? CNMF_F64 : CNMF_F32;
+  W* ach = (W*)L.ach;
+  W* aht = (W*)L.aht;
+  W* yc = (W*)L.yc;
+  W* xh = (W*)L.xh;
+  // A-check = A R^T (m x d), A-hat^T = A^T L (n x d): one read of A each
+  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, ach, d, d, status};
+  CNMF_TRY(launch_prod(pc, L.prod_ws, L.prod_bytes, s));
+  ProdArgs ph{A, a_type, m, n, lda, true, Lm, d, d, aht, d, d, status};
+  CNMF_TRY(launch_prod(ph, L.prod_ws, L.prod_bytes, s));
+  for (int it = 0; it < iters; ++it) {
+    // Y-check = Y R^T (r x d)
+    ProdArgs py{Y, w, r, n, n, false, Rt, d, d, yc, d, d, status};
+    CNMF_TRY(launch_prod(py, L.prod_ws, L.prod_bytes, s));
+    // X: row i = argmin_{x >= 0} ||A-check[i] - x Y-check||; B = Y-check^T
+    CNMF_TRY(nnls_run<W>(ach, d, m, d, nullptr, 0, 0, nullptr, yc, 1, d, r,
+                         max_sweeps, tol, X, 1, r, unconverged, L.nn, status,
+                         s));
+    // X-hat = L^T X (d x r)
+    ProdArgs px{Lm, w, m, d, d, true, X, r, r, xh, r, r, status};
+    CNMF_TRY(launch_prod(px, L.prod_ws, L.prod_bytes, s));
+    // Y: column j = argmin_{y >= 0} ||A-hat[:, j] - X-hat y||; B = X-hat
+    CNMF_TRY(nnls_run<W>(aht, d, n, d, nullptr, 0, 0, nullptr, xh, r, 1, r,
+                         max_sweeps, tol, Y, n, 1, unconverged, L.nn, status,
+                         s));
+  }
   return CNMF_OK;
 }
 
@@ -316,8 +405,45 @@ extern "C" cnmf_status snmf_right_factor(const void* Rhat_t, cnmf_dtype w_type,
   if (ws_bytes < L.bytes) return CNMF_E_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   if (w_type == CNMF_F64)
-    return nnls_run<double>(Rhat_t, n, d, ld, anchors, r, max_sweeps, tol, Y,
-                            ldy, unconverged, L, dev_status, s);
-  return nnls_run<float>(Rhat_t, n, d, ld, anchors, r, max_sweeps, tol, Y,
-                         ldy, unconverged, L, dev_status, s);
+    return nnls_run<double>((const double*)Rhat_t, ld, n, d,
+                            (const double*)Rhat_t, n, ld, anchors, nullptr, 0,
+                            0, r, max_sweeps, tol, (double*)Y, ldy, 1,
+                            unconverged, L, dev_status, s);
+  return nnls_run<float>((const float*)Rhat_t, ld, n, d, (const float*)Rhat_t,
+                         n, ld, anchors, nullptr, 0, 0, r, max_sweeps, tol,
+                         (float*)Y, ldy, 1, unconverged, L, dev_status, s);
+}
+
+extern "C" size_t cnmf_factor_als_workspace(int64_t m, int64_t n, int32_t r,
+                                            int32_t d, cnmf_dtype a_type) {
+  if (m < 1 || n < 1 || d < 1 || d > 128 || r < 1 || r > 64 || r > d ||
+      (a_type != CNMF_F64 && a_type != CNMF_F32 && a_type != CNMF_BF16))
+    return 0;
+  return als_layout(nullptr, m, n, r, d, a_type).bytes;
+}
+
+extern "C" cnmf_status cnmf_factor_als(const void* A, cnmf_dtype a_type,
+                                       int64_t m, int64_t n, int64_t lda,
+                                       const void* L, const void* Rt,
+                                       int32_t r, int32_t d, int32_t iters,
+                                       int32_t max_sweeps, double tol, void* X,
+                                       void* Y, int32_t* unconverged, void* ws,
+                                       size_t ws_bytes, int32_t* dev_status,
+                                       cnmf_stream_t stream) {
+  if ((a_type != CNMF_F64 && a_type != CNMF_F32 && a_type != CNMF_BF16) ||
+      !A || !L || !Rt || !X || !Y || !ws || m < 1 || n < 1 || lda < n ||
+      d < 1 || d > 128 || d > m || d > n || r < 1 || r > 64 || r > d ||
+      iters < 0 || max_sweeps < 1 || !(tol >= 0.0))
+    return CNMF_E_INVALID_ARG;
+  AlsLayout lay = als_layout(ws, m, n, r, d, a_type);
+  if (ws_bytes < lay.bytes) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a_type == CNMF_F64)
+    return als_run<double>(A, a_type, m, n, lda, (const double*)L,
+                           (const double*)Rt, r, d, iters, max_sweeps, tol,
+                           (double*)X, (double*)Y, unconverged, lay,
+                           dev_status, s);
+  return als_run<float>(A, a_type, m, n, lda, (const float*)L,
+                        (const float*)Rt, r, d, iters, max_sweeps, tol,
+                        (float*)X, (float*)Y, unconverged, lay, dev_status, s);
 }
