@@ -118,3 +118,33 @@ def test_right_factor_invalid_arguments(lib):
     assert lib.snmf_right_factor(None, 1, 100, 10, 10, fake, 4, 10, 1e-6, fake,
                                  100, None, fake, 1 << 30, None, None) == E
     assert lib.snmf_right_factor_workspace(100, 10, 11, 1) == 0
+
+
+def test_als_and_gaussian_compression_invalid_arguments(lib):
+    E = 1
+    f = C.c_void_p(16)
+    # cnmf_factor_als(A, a_type, m, n, lda, L, Rt, r, d, iters, sweeps, tol,
+    #                 X, Y, unconverged, ws, ws_bytes, status, stream)
+    def als(**kw):
+        a = dict(m=100, n=80, lda=80, r=4, d=10, iters=2, sweeps=10, tol=1e-6)
+        a.update(kw)
+        return lib.cnmf_factor_als(f, 1, a["m"], a["n"], a["lda"], f, f, a["r"],
+                                   a["d"], a["iters"], a["sweeps"], a["tol"], f,
+                                   f, None, f, 1 << 30, None, None)
+    assert als(r=11) == E            # r > d
+    assert als(d=81, r=4) == E       # d > n
+    assert als(lda=79) == E
+    assert als(iters=-1) == E
+    assert als(sweeps=0) == E
+    assert als(tol=-1.0) == E
+    assert lib.cnmf_factor_als_workspace(100, 80, 11, 10, 1) == 0
+    # cnmf_compress_gaussian(A, a_type, m, n, lda, d, seed, L, Rt, Atilde,
+    #                        ws, ws_bytes, status, stream)
+    assert lib.cnmf_compress_gaussian(f, 1, 100, 80, 80, 0, 1, f, f, f, f,
+                                      1 << 30, None, None) == E
+    assert lib.cnmf_compress_gaussian(f, 1, 100, 80, 80, 81, 1, f, f, f, f,
+                                      1 << 30, None, None) == E
+    assert lib.cnmf_compress_gaussian(None, 1, 100, 80, 80, 8, 1, f, f, f, f,
+                                      1 << 30, None, None) == E
+    assert lib.cnmf_compress_gaussian(f, 1, 100, 80, 80, 8, 1, f, f, f, f,
+                                      16, None, None) == 2   # CNMF_E_WORKSPACE
