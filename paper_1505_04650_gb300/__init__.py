@@ -357,7 +357,13 @@ def snmf_right_factor(Rhat_t: torch.Tensor, anchors: torch.Tensor,
     `anchors` (Rhat_t n x d as snmf_select returns it)."""
     n, d = Rhat_t.shape
     w = Rhat_t.dtype
+    if w not in (torch.float32, torch.float64):
+        raise ValueError(f"Rhat_t: expected float32 or float64, got {w}")
     _dense(Rhat_t, (n, d), w, "Rhat_t")
+    if anchors.dtype != torch.int64 or not anchors.is_contiguous() \
+            or anchors.device != Rhat_t.device or anchors.dim() != 1:
+        raise ValueError("anchors: expected a contiguous int64 vector on "
+                         "Rhat_t's device")
     r = anchors.numel()
     dev = Rhat_t.device
     Y = torch.empty(r, n, dtype=w, device=dev)

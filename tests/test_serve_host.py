@@ -42,3 +42,4 @@ def test_autotune_buckets():
     assert bucket(1, 1, 1, 1) == "m1024_n1024_r16_d32"
     assert bucket(1024, 1025, 16, 33) == "m1024_n2048_r16_d64"
     assert bucket(3000, 200, 20, 30) == bucket(2100, 1, 17, 31)
+
