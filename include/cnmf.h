@@ -17,9 +17,16 @@
  *     R is stored transposed as Rt = R^T (n x d), V as Vt = V^T (n x r),
  *     Phi as Phit = Phi^T (n x r), Rhat as Rhat_t = (Q^T A)^T (n x d).
  *   - Every pointer is a DEVICE pointer owned by the caller, unless stated.
- *     The library never allocates device memory and keeps no global mutable
- *     state; scratch space is the caller's workspace `ws`, whose size comes
- *     from the matching *_workspace() query (256-byte aligned pointer).
+ *     The library never allocates device memory; scratch space is the
+ *     caller's workspace `ws`, whose size comes from the matching
+ *     *_workspace() query (256-byte aligned pointer).  Its only state:
+ *     per-device caches filled on first use (SM count, opt-in shared
+ *     memory, kernel shared-memory limits raised once per device, the
+ *     driver's tensor-map encoder, the device address of
+ *     cnmf_residual_noalloc's static scratch), each guarded for
+ *     concurrent first calls; the calling host thread's CTA limit
+ *     (cnmf_set_thread_cta_limit); and the text of that thread's last
+ *     CUDA error (cnmf_last_error).
  *   - All work is enqueued asynchronously on `stream` (a cudaStream_t).
  *   - Host-detected errors (bad sizes, NULL pointers, small workspace,
  *     launch failures) are returned immediately with NOTHING enqueued,
@@ -126,16 +133,25 @@ cnmf_status cnmf_philox_words(uint64_t seed, uint32_t stream_id,
 
 /* One two-sided product pass over A (Alg. 1 power scheme, Sec. III):
  *   Zm = A X   (m x k, from X n x k)     and/or
- *   Zn = A^T Y (n x k, from Y m x k),
- * reading A once per product.  X, Y, Zm, Zn are W-typed with row pitch k.
- * Pass X = NULL / Zm = NULL (or Y = NULL / Zn = NULL) to skip one side.
- * 1 <= k <= 128.  FP64 / FP32 A: CUDA-core FMA, exact products rounded in
- * W.  BF16 A (16-byte aligned, lda a multiple of 8): tensor cores
- * (tcgen05, FP32 accumulate) with X / Y split into bf16 hi + lo parts, so
- * the products carry an extra relative error of at most 2^-18 of |A||X|;
- * setting the environment variable CNMF_NO_TENSOR_CORES selects the
- * CUDA-core kernel instead.  dev_status (optional): CNMF_E_TIMEOUT if a
- * bounded pipeline wait expired. */
+ *   Zn = A^T Y (n x k, from Y m x k).
+ * X, Y, Zm, Zn are W-typed with row pitch k.  Pass X = NULL / Zm = NULL
+ * (or Y = NULL / Zn = NULL) to skip one side.  1 <= k <= 128.
+ *   FP64 A (and A whose base or row pitch is not 16-byte aligned): CUDA-core
+ *   FMA, one read of A per product, exact products rounded in W.
+ *   FP32 / BF16 A: tensor cores (tcgen05, FP32 accumulation).  For k <= 32
+ *   both products come from ONE read of A (fused pass): each 128 x 128
+ *   tile feeds A X (tile K-major) and A^T Y (the same bytes MN-major); FP32
+ *   A is split in shared memory into bf16 hi + lo parts (|A - hi - lo| <=
+ *   2^-18 |A|).  For k > 32 each product reads A once (FP32 A as 3xTF32).
+ *   X / Y are split into bf16 (3xTF32: TF32) hi + lo parts.  The products
+ *   carry an extra relative error of at most 2^-17 (BF16 A) or 2^-16 (FP32
+ *   A: the split of A and the dropped A_lo Y_lo term) of |A||X| besides
+ *   FP32 accumulation.  Environment: CNMF_UNFUSED_SKETCH selects one read per
+ *   product for k <= 32 too; CNMF_NO_TENSOR_CORES selects the CUDA-core
+ *   kernel.
+ * Results do not depend on timing (partial sums are added in a fixed
+ * order).  dev_status (optional): CNMF_E_TIMEOUT if a bounded pipeline
+ * wait expired. */
 size_t cnmf_sketch_workspace(int64_t m, int64_t n, int32_t k,
                              cnmf_dtype a_type);
 cnmf_status cnmf_sketch_pass(const void* A, cnmf_dtype a_type, int64_t m,
@@ -163,7 +179,8 @@ cnmf_status cnmf_orth(void* Y, cnmf_dtype w_type, int64_t rows, int32_t k,
  *   r, d    target rank and sketch size d = r + r_ov, 1 <= r <= d <=
  *           min(m, n), d <= 128.
  *   q       power iterations (Alg. 1 exponent w), 0 <= q <= 64.  The
- *           compression reads A 2q + 2 times.
+ *           compression reads A 2q + 2 times when d <= 32 and A is FP32 or
+ *           BF16 (2q + 1 fused passes and A-check), else 4q + 3 times.
  *   seed    Philox seed for Omega (stream 0, n x d, left chain) and Psi
  *           (stream 1, m x d, right chain), used when Omega/Psi are NULL.
  *   Omega, Psi  optional caller test matrices (W-typed, n x d and m x d).

@@ -68,6 +68,25 @@ bool set_max_smem(const void* func, size_t bytes) {
   return true;
 }
 
+bool ensure_max_smem(const void* func, size_t bytes) {
+  struct Done { const void* f; int dev; size_t bytes; };
+  static std::mutex mu;
+  static Done done[256];
+  static int ndone = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  for (int i = 0; i < ndone; ++i)
+    if (done[i].f == func && done[i].dev == dev && done[i].bytes >= bytes)
+      return true;
+  if (!set_max_smem(func, bytes)) return false;
+  if (ndone < 256) done[ndone++] = Done{func, dev, bytes};
+  return true;
+}
+
 static thread_local char g_err[320];
 
 void record_cuda_error(cudaError_t e, const char* file, int line) {

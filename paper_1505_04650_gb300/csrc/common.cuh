@@ -258,6 +258,10 @@ int max_smem_optin();                // opt-in shared memory per block (bytes)
 // pending error behind; returns false if `bytes` is not allowed.
 bool set_max_smem(const void* func, size_t bytes);
 size_t static_smem(const void* func);  // static shared memory of a kernel
+// set_max_smem once per (kernel, device): the attribute belongs to the
+// current device's context, so a process that uses several GPUs raises it
+// on each of them.  Thread-safe; false if `bytes` is not allowed.
+bool ensure_max_smem(const void* func, size_t bytes);
 // Remembers (per host thread) the CUDA error behind the last CNMF_E_CUDA.
 void record_cuda_error(cudaError_t e, const char* file, int line);
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -75,6 +75,22 @@ static CompressLayout compress_layout(void* ws, int64_t m, int64_t n, int d,
   return L;
 }
 
+// A-check = A R^T into the layout's m x KP panel: the one-sided form of the
+// fused pass where it applies, else the product kernels.
+static cnmf_status acheck_product(const void* A, cnmf_dtype a_type, int64_t m,
+                                  int64_t n, int64_t lda, const void* Rt,
+                                  int d, const CompressLayout& lay,
+                                  int32_t* dev_status, cudaStream_t s) {
+  if (fused_applicable(A, a_type, m, n, lda, d, true, false)) {
+    FusedArgs fa{A, a_type, m, n, lda, Rt, d, nullptr, 0, d, lay.acheck,
+                 lay.KP, nullptr, 0, dev_status};
+    return launch_fused(fa, lay.prod_ws, lay.prod_bytes, s);
+  }
+  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, lay.KP, d,
+              dev_status};
+  return launch_prod(pc, lay.prod_ws, lay.prod_bytes, s);
+}
+
 }  // namespace cnmf
 
 using namespace cnmf;
@@ -96,6 +112,10 @@ extern "C" cnmf_status cnmf_sketch_pass(const void* A, cnmf_dtype a_type,
     return CNMF_E_INVALID_ARG;
   if (ws_bytes < prod_workspace(m, n, k, a_type)) return CNMF_E_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
+  if (fused_applicable(A, a_type, m, n, lda, k, X != nullptr, Y != nullptr)) {
+    FusedArgs fa{A, a_type, m, n, lda, X, k, Y, k, k, Zm, k, Zn, k, dev_status};
+    return launch_fused(fa, ws, ws_bytes, s);
+  }
   if (X) {
     ProdArgs pa{A, a_type, m, n, lda, false, X, k, k, Zm, k, k, dev_status};
     CNMF_TRY(launch_prod(pa, ws, ws_bytes, s));
@@ -166,14 +186,22 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
   void* mb[2] = {lay.m0, lay.m1};
   void* nb[2] = {lay.n0, lay.n1};
   const int T = 2 * q + 1;
+  const bool fused = fused_applicable(A, a_type, m, n, lda, d);
   for (int t = 0; t < T; ++t) {
     const bool last = (t == T - 1);
     void* zm = mb[t & 1];
     void* zn = nb[t & 1];
-    ProdArgs pa{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d, dev_status};
-    CNMF_TRY(launch_prod(pa, lay.prod_ws, lay.prod_bytes, s));
-    ProdArgs pt{A, a_type, m, n, lda, true, Y, ldy, d, zn, KP, d, dev_status};
-    CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
+    if (fused) {
+      // both products of the pass from one read of A
+      FusedArgs fa{A, a_type, m, n, lda, X, ldx, Y, ldy, d, zm, KP, zn, KP,
+                   dev_status};
+      CNMF_TRY(launch_fused(fa, lay.prod_ws, lay.prod_bytes, s));
+    } else {
+      ProdArgs pa{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d, dev_status};
+      CNMF_TRY(launch_prod(pa, lay.prod_ws, lay.prod_bytes, s));
+      ProdArgs pt{A, a_type, m, n, lda, true, Y, ldy, d, zn, KP, d, dev_status};
+      CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
+    }
     OrthPanel op[2] = {{zm, m, KP, last ? L : zm, last ? d : KP},
                        {zn, n, KP, last ? Rt : zn, last ? d : KP}};
     // the last pass gives L and R^T: the unique thin Q (CholeskyQR2); in
@@ -187,8 +215,7 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
     Y = zm; ldy = KP;
   }
   // A-check = A R^T (m x d), then A-tilde = L^T A-check (d x d)
-  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, KP, d, dev_status};
-  CNMF_TRY(launch_prod(pc, lay.prod_ws, lay.prod_bytes, s));
+  CNMF_TRY(acheck_product(A, a_type, m, n, lda, Rt, d, lay, dev_status, s));
   CNMF_TRY(launch_cross(L, d, lay.acheck, KP, m, d, w, Atilde, d, lay.orth_ws,
                         lay.orth_bytes, s));
   return CNMF_OK;
@@ -219,8 +246,7 @@ extern "C" cnmf_status cnmf_compress_gaussian(const void* A, cnmf_dtype a_type,
   CNMF_TRY(launch_gaussian(seed, 0, n * (int64_t)d, w, Rt, s));
   CNMF_TRY(launch_scale(Rt, n * (int64_t)d, w, c, s));
   // A-check = A R^T (m x d), then A-tilde = L^T A-check (d x d)
-  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, lay.acheck, KP, d, dev_status};
-  CNMF_TRY(launch_prod(pc, lay.prod_ws, lay.prod_bytes, s));
+  CNMF_TRY(acheck_product(A, a_type, m, n, lda, Rt, d, lay, dev_status, s));
   CNMF_TRY(launch_cross(L, d, lay.acheck, KP, m, d, w, Atilde, d, lay.orth_ws,
                         lay.orth_bytes, s));
   return CNMF_OK;

@@ -38,6 +38,31 @@ cnmf_status launch_prod_fixup_f32(void* Z, int64_t ldz, int kz, int64_t P,
                                   int64_t chunks, int64_t G, int KP,
                                   cudaStream_t s);
 
+// ---- fused two-sided pass (fused.cu): Zm = A X (m x k, pitch ldzm) and
+//      Zn = A^T Y (n x k, pitch ldzn) from one read of A; FP32 or BF16 A,
+//      k <= 32, A 16-byte aligned with 16-byte row pitch; X = NULL (Y = NULL)
+//      leaves that product out ----------------------------------------------
+struct FusedArgs {
+  const void* A;
+  cnmf_dtype a_type;
+  int64_t m, n, lda;
+  const void* X;       // n x k, pitch ldx (FP32)
+  int64_t ldx;
+  const void* Y;       // m x k, pitch ldy (FP32)
+  int64_t ldy;
+  int k;
+  void* Zm;
+  int64_t ldzm;
+  void* Zn;
+  int64_t ldzn;
+  int32_t* status;
+};
+size_t fused_workspace(int64_t m, int64_t n, int k, cnmf_dtype a_type);
+bool fused_applicable(const void* A, cnmf_dtype a_type, int64_t m, int64_t n,
+                      int64_t lda, int k, bool has_x = true, bool has_y = true);
+cnmf_status launch_fused(const FusedArgs& a, void* ws, size_t ws_bytes,
+                         cudaStream_t s);
+
 // ---- CholeskyQR2 on up to two tall panels at once --------------------------
 struct OrthPanel {
   void* Y;       // in: rows x k panel (pitch ld); out: Q (pitch ldo) in Q

@@ -256,18 +256,19 @@ __global__ void k_prod_fixup(W* __restrict__ Z, int64_t ldz, int kz, int64_t P,
 template <typename TA, typename W, int KP, bool TRANS>
 static int sk_grid_slots() {
   typedef SkCfg<TA, W, KP, TRANS> C;
-  static int slots = 0;
+  static int resident = 0;   // CTAs per SM (the same on every GB300)
   static std::once_flag once;
-  std::call_once(once, [] {
-    auto kern = k_prod<TA, W, KP, TRANS>;
-    set_max_smem((const void*)kern, C::SMEM);
+  auto kern = k_prod<TA, W, KP, TRANS>;
+  ensure_max_smem((const void*)kern, C::SMEM);   // per device
+  std::call_once(once, [kern] {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SK_NT,
                                                       C::SMEM) != cudaSuccess)
       (void)cudaGetLastError();
-    slots = std::min(4, std::max(1, per_sm)) * num_sms();
+    resident = std::min(4, std::max(1, per_sm));
   });
-  return slots;
+  // num_sms() follows the calling thread's CTA limit, so it is read per call
+  return resident * num_sms();
 }
 
 template <typename TA, typename W, int KP, bool TRANS>
@@ -321,7 +322,10 @@ size_t prod_workspace(int64_t m, int64_t n, int k, cnmf_dtype a_type) {
   // two partial tiles per CTA; at most 4 resident CTAs per SM.
   size_t w = a_type == CNMF_F64 ? 8 : 4;
   size_t b = (size_t)4 * num_sms() * 2 * SK_BP * prod_kp(k) * w + 256;
-  if (a_type != CNMF_F64) b = std::max(b, tc_workspace(m, n, k));
+  if (a_type != CNMF_F64) {
+    b = std::max(b, tc_workspace(m, n, k));
+    b = std::max(b, fused_workspace(m, n, k, a_type));
+  }
   return b;
 }
 

@@ -46,11 +46,15 @@ def rel(a, b) -> float:
 def product_bound(storage, s):
     """Relative bound (times |A| |B|) of a length-s product with A stored
     as `storage`: FP64 -> (s + 2) u; FP32 and BF16 run on the tensor cores
-    with FP32 accumulation (2u per add) plus the operand-split residual
-    (3xTF32: 2^-19; bf16 hi + lo of the thin operand: 2^-17)."""
+    with FP32 accumulation (2u per add) plus the operand-split residual:
+    the thin operand as bf16 hi + lo leaves at most 2^-18 of it (BF16 A:
+    2^-17 covers it); FP32 A split the same way in the fused pass leaves
+    another 2^-18 and the dropped A_lo B_lo term a third (3xTF32, the
+    product kernel for wider panels, leaves less: 2^-19); 2^-16 covers
+    both."""
     u = unit(storage)
     if storage == "bf16":
         return (s + 2) * 2 * u + 2.0 ** -17
     if storage == "f32":
-        return (s + 2) * 2 * u + 2.0 ** -19
+        return (s + 2) * 2 * u + 2.0 ** -16
     return (s + 2) * u
