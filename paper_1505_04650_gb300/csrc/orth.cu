@@ -595,18 +595,16 @@ static size_t apply_smem() {
   return std::max(stage, sizeof(double) * GramMap<KP, true>::RED);
 }
 
+// The attribute belongs to the current device's context: raised once per
+// (kernel, device).
 template <typename W, int KP>
 static void set_smem_attrs() {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    size_t fin = finish_smem<W, KP>();
-    set_max_smem((const void*)k_finish<W, KP>, fin);
-    size_t ap = apply_smem<W, KP>();
-    set_max_smem((const void*)k_gram<W, KP, false>, gram_smem<W, KP, false>());
-    set_max_smem((const void*)k_gram<W, KP, true>, gram_smem<W, KP, true>());
-    set_max_smem((const void*)k_apply<W, KP, true>, ap);
-    set_max_smem((const void*)k_apply<W, KP, false>, ap);
-  });
+  ensure_max_smem((const void*)k_finish<W, KP>, finish_smem<W, KP>());
+  const size_t ap = apply_smem<W, KP>();
+  ensure_max_smem((const void*)k_gram<W, KP, false>, gram_smem<W, KP, false>());
+  ensure_max_smem((const void*)k_gram<W, KP, true>, gram_smem<W, KP, true>());
+  ensure_max_smem((const void*)k_apply<W, KP, true>, ap);
+  ensure_max_smem((const void*)k_apply<W, KP, false>, ap);
 }
 
 template <typename W, int KP>

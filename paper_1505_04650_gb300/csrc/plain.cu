@@ -122,10 +122,7 @@ static cnmf_status rows_launch(int64_t rows, int r, const void* Z, void* P1,
                                void* P2, void* X, const void* rinv, double c,
                                double xi, cudaStream_t s) {
   const size_t smem = sizeof(W) * (RP * RP + 2 * PL_ROWS * (RP + 4));
-  static std::once_flag once;
-  std::call_once(once, [smem] {
-    set_max_smem((const void*)k_plain_rows<W, RP>, smem);
-  });
+  ensure_max_smem((const void*)k_plain_rows<W, RP>, smem);
   int G = (int)std::max<int64_t>(
       1, std::min<int64_t>(2 * num_sms(), ceil_div(rows, PL_ROWS)));
   k_plain_rows<W, RP><<<G, PL_NT, smem, s>>>(rows, r, (const W*)Z, (W*)P1,

@@ -110,10 +110,10 @@ static cnmf_status run_res(const void* A, int64_t m, int64_t n, int64_t lda,
                            void* ws, cudaStream_t s) {
   const int G = res_grid(m, n);
   const size_t smem = sizeof(W) * 2 * RS_T * (r + 1);
-  static std::once_flag once;
-  std::call_once(once, [] {
-    set_max_smem((const void*)k_residual<TA, W>, sizeof(W) * 2 * RS_T * 129);
-  });
+  // raised once per (kernel, device): a second GPU needs its own raise
+  if (!ensure_max_smem((const void*)k_residual<TA, W>,
+                       sizeof(W) * 2 * RS_T * 129))
+    return CNMF_E_INVALID_ARG;
   double* part = (double*)ws;
   k_residual<TA, W><<<G, RS_NT, smem, s>>>((const TA*)A, m, n, lda,
                                            (const W*)U, (const W*)Vt, r, part);
