@@ -132,8 +132,13 @@ __global__ void __launch_bounds__(NN_NT)
            const W* __restrict__ G, const W* __restrict__ gd,
            const W* __restrict__ Gi, int max_sweeps, W tol,
            W* __restrict__ Y, int64_t ysj, int64_t ysc,
-           int32_t* __restrict__ unconverged) {
+           int32_t* __restrict__ unconverged,
+           const int32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the set-up kernel found an anchor index out of range (or an earlier
+  // step failed): G and its inverse were not formed, so there is nothing to
+  // solve; Y is left unwritten and the status word already says why
+  if (status && *reinterpret_cast<const volatile int32_t*>(status) != 0) return;
   W* Gs = reinterpret_cast<W*>(smem_raw);       // RMAX x RMAX
   W* Gis = Gs + RMAX * RMAX;                     // RMAX x RMAX
   W* gds = Gis + RMAX * RMAX;                    // RMAX
@@ -191,11 +196,15 @@ __global__ void __launch_bounds__(NN_NT)
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) {
         const W v = h[j] > W(0) ? fabs(g[j]) : (g[j] < W(0) ? -g[j] : W(0));
-        pg = v > pg ? v : pg;
+        pg = (v > pg || v != v) ? v : pg;   // a NaN stays in pg
       }
-      conv = !(pg > lim);   // NaN never counts as converged
+      // NaN (from NaN or Inf in b or G) is never converged: the column
+      // stops at once and is counted as unconverged
+      conv = pg <= lim;
+      const bool bad = pg != pg;
       // the warp runs until every lane is done (lanes past n count as done)
-      if (__all_sync(0xffffffffu, conv || !have) || sw == max_sweeps) break;
+      if (__all_sync(0xffffffffu, conv || bad || !have) || sw == max_sweeps)
+        break;
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) {
         if (j < r) {
@@ -223,7 +232,7 @@ static cnmf_status nnls_launch(int grid, const W* Bt, int64_t n, int r,
                                int rp, const W* G, const W* gd, const W* Gi,
                                int max_sweeps, W tol, W* Y, int64_t ysj,
                                int64_t ysc, int32_t* unconverged,
-                               cudaStream_t s) {
+                               const int32_t* status, cudaStream_t s) {
   constexpr size_t smem = nnls_smem<W, RMAX>();
   if (cudaFuncSetAttribute((const void*)k_nnls<W, RMAX>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -231,7 +240,7 @@ static cnmf_status nnls_launch(int grid, const W* Bt, int64_t n, int r,
     return CNMF_E_CUDA;
   k_nnls<W, RMAX><<<grid, NN_NT, smem, s>>>(Bt, n, r, rp, G, gd, Gi,
                                             max_sweeps, tol, Y, ysj, ysc,
-                                            unconverged);
+                                            unconverged, status);
   CNMF_CUDA(cudaGetLastError());
   return CNMF_OK;
 }
@@ -298,14 +307,14 @@ static cnmf_status nnls_run(const W* M, int64_t ldm, int64_t rows, int d,
   if (r <= 16)
     return nnls_launch<W, 16>(grid, (const W*)L.bt, rows, r, rp, (const W*)L.G,
                               (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, Y,
-                              ysj, ysc, unconverged, s);
+                              ysj, ysc, unconverged, status, s);
   if (r <= 32)
     return nnls_launch<W, 32>(grid, (const W*)L.bt, rows, r, rp, (const W*)L.G,
                               (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, Y,
-                              ysj, ysc, unconverged, s);
+                              ysj, ysc, unconverged, status, s);
   return nnls_launch<W, 64>(grid, (const W*)L.bt, rows, r, rp, (const W*)L.G,
                             (const W*)L.gd, (const W*)L.Gi, max_sweeps, t, Y,
-                            ysj, ysc, unconverged, s);
+                            ysj, ysc, unconverged, status, s);
 }
 
 struct AlsLayout {
