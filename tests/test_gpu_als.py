@@ -20,11 +20,14 @@ from gpu_util import need_gpu, to_np, to_dev, wdt
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_als_matches_oracle(storage):
+@pytest.mark.parametrize("storage,r,d,iters", [("f64", 4, 10, 3),
+                                               ("f32", 4, 10, 3),
+                                               ("f64", 8, 16, 20),
+                                               ("f32", 8, 16, 20)])
+def test_als_matches_oracle(storage, r, d, iters):
     torch = need_gpu()
     import paper_1505_04650_gb300 as cn
-    m, n, r, d, iters = 300, 220, 4, 10, 3
+    m, n = 300, 220
     As = synth.as_storage(synth.lowrank(m, n, r, 0.02, 21), storage)
     A = synth.widen(As, storage)
     Om, Ps = ophil.test_matrices(22, m, n, d)
@@ -51,3 +54,5 @@ def test_als_matches_oracle(storage):
     bar = 1e-7 if storage == "f64" else 1e-3
     assert ex <= bar and ey <= bar
     assert Xg.min() >= 0 and Yg.min() >= 0
+    # every NNLS column met the stopping rule inside the sweep cap
+    assert int(unconv.item()) == 0

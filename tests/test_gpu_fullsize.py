@@ -13,7 +13,11 @@ compute one by one (sampled rows and columns of the products).
   for BF16 and FP32 storage: sampled rows of A X and columns of A^T Y
   against FP64 within the product bound;
 * the mixed-precision error statement: projector and objective of the
-  BF16 / FP32 paths against the FP64 oracle at a size it can run.
+  BF16 / FP32 paths against the FP64 oracle at a size it can run;
+* parity with the FP64 oracle at the bench's size itself: the oracle's
+  compression of the same FP32 matrix (same Omega, Psi), the rank-r signal
+  projector (1e-5), the signal singular values of A-tilde, and 20 ADMM
+  sweeps from the oracle's L, R^T, A-tilde (factors 1e-4).
 """
 import math
 
@@ -146,5 +150,65 @@ def test_mixed_precision_errors_vs_oracle(storage, q):
     if storage == "bf16":
         msg += f"  vs FP64 A: rho {ores.rel_residual(A64, to_np(U), to_np(Vt).T):.4e}"
     print(msg)
-    assert ep <= 1e-4
+    assert ep <= 1e-5
     assert eo <= 1e-3
+
+
+def _signal_basis(L, A, r):
+    """Top-r left singular vectors of L L^T A, as L W_r from the SVD of the
+    d x n matrix L^T A (the m x m projector itself is not formed)."""
+    W, _, _ = np.linalg.svd(L.T @ A, full_matrices=False)
+    return L @ W[:, :r]
+
+
+def _projector_distance(U1, U2):
+    """||U1 U1^T - U2 U2^T||_F / ||U2 U2^T||_F for orthonormal U1, U2 of
+    rank r: sqrt(2) ||U1 - U2 (U2^T U1)||_F / sqrt(r), free of the
+    cancellation in 2 r - 2 ||U2^T U1||_F^2."""
+    r = U2.shape[1]
+    return float(np.sqrt(2.0) * np.linalg.norm(U1 - U2 @ (U2.T @ U1)) / np.sqrt(r))
+
+
+def test_cnmf_bench_size_matches_oracle():
+    """m = 20000, n = 10000, r = 20, d = 30, q = 4, FP32: the workload the
+    bench times, compared with the FP64 oracle on the values the GPU
+    reads."""
+    torch = need_gpu()
+    import paper_1505_04650_gb300 as cn
+    m, n, r, d, q = 20000, 10000, 20, 30, 4
+    A = synth.lowrank(m, n, r, 0.01, 1001, dtype=np.float32)
+    Aw = A.astype(np.float64)
+    Om, Ps = ophil.test_matrices(2001, m, n, d)
+    L0, Rt0, _, At0 = ocomp.compress(Aw, Om, Ps, q)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Ad = torch.from_numpy(A).cuda()
+    L, Rt, At, _ = cn.cnmf_compress(Ad, r, d, q, 2001, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    Lg, Rg, Ag = to_np(L), to_np(Rt), to_np(At)
+    # signal projectors of both sides
+    ep_l = _projector_distance(_signal_basis(Lg, Aw, r), _signal_basis(L0, Aw, r))
+    ep_r = _projector_distance(_signal_basis(Rg, Aw.T, r), _signal_basis(Rt0, Aw.T, r))
+    # A-tilde: its signal singular values are basis-free
+    sg = np.linalg.svd(Ag, compute_uv=False)
+    so = np.linalg.svd(At0, compute_uv=False)
+    es = float(np.abs(sg[:r] - so[:r]).max() / so[0])
+    print(f"signal projector L {ep_l:.2e}, R {ep_r:.2e}; A-tilde singular values {es:.2e}")
+    assert ep_l <= 1e-5 and ep_r <= 1e-5
+    assert es <= 1e-5
+    # 20 sweeps from the oracle's compression (rounded to the FP32 inputs)
+    f32 = lambda x: x.astype(np.float32).astype(np.float64)
+    Lf, Rtf, Atf = f32(L0), f32(Rt0), f32(At0)
+    U0, V0 = synth.init_factors(m, n, r, 3001)
+    U0, V0 = f32(U0), f32(V0)
+    lam = float(np.linalg.norm(Atf)) / r
+    dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    U, Vt, _, _ = cn.cnmf_factor(dev(Lf), dev(Rtf), dev(Atf), dev(U0),
+                                 dev(V0.T.copy()), lam, lam, 20, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = oadmm.admm(Lf, Rtf, Atf, U0, V0, lam=lam, phi=lam, iters=20)
+    eu = rel(to_np(U), ref.U)
+    ev = rel(to_np(Vt).T, ref.V)
+    print(f"20 sweeps: U {eu:.2e}, V {ev:.2e}")
+    assert eu <= 1e-4 and ev <= 1e-4

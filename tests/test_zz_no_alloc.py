@@ -5,7 +5,9 @@ memory (a plugin whose host application owns all device allocations, code
 running while another allocator has reserved the device, a latency-critical
 loop that must not reach cudaMalloc).  Its scratch is a static device array
 inside the library, shared by every call, so two calls in a row must both
-agree with the workspace-taking entry point.  This file is collected last.
+agree with the workspace-taking entry point, and the second call must leave
+the device's allocated and free memory unchanged.  This file is collected
+last.
 """
 import ctypes as C
 
@@ -38,16 +40,26 @@ def test_residual_noalloc_matches_workspace_entry_point(storage, m, n, r):
     wt = _lib.CNMF_F64 if storage == "f64" else _lib.CNMF_F32
     s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     tol = 1e-12 if storage == "f64" else 2e-5
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    host = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    mem = []
     for call in range(2):
-        out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+        out.fill_(-1.0)
         rc = lib.cnmf_residual_noalloc(
             C.c_void_p(Ad.data_ptr()), dt[storage], m, n, Ad.stride(0),
             C.c_void_p(U.data_ptr()), C.c_void_p(Vt.data_ptr()), wt, r,
             C.c_void_p(out.data_ptr()), s)
         assert rc == 0, lib.cnmf_last_error().decode()
-        got = out.cpu().numpy()
+        host.copy_(out)
+        torch.cuda.synchronize()
+        # what the process holds on the device after the call: PyTorch's
+        # allocations and the driver's free-memory count
+        mem.append((torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]))
+        got = host.numpy()
         assert abs(got[1] - ref[1]) <= tol * ref[1], call
         assert abs(got[0] - ref[0]) <= tol * ref[1], call
+    # the second call allocated nothing, through PyTorch or the driver
+    assert mem[1] == mem[0], mem
 
 
 def test_residual_noalloc_rejects_bad_arguments():
