@@ -165,15 +165,16 @@ def run_reference(args):
     return 0
 
 
-def launches_per_step(q, chunks_gt1=True):
+def launches_per_step(q):
     """Library kernel launches of one step (compress + one factor launch),
-    for FP32 A on the tensor-core product path: each product is a B-panel
-    pack, the product kernel and (split tiles) the fix-up; between products
-    one CholeskyQR sweep of both panels (gram, finish, apply), CholeskyQR2
-    (gram, finish, apply, finish, apply) after the last pass."""
-    prod = 3 if chunks_gt1 else 2
+    for FP32 A with d <= 32 (the fused pass): two Gaussian panels; per pass
+    the panel pack, the fused two-sided kernel and the partial-slot sum;
+    between passes one CholeskyQR sweep of both panels (gram, finish,
+    apply), CholeskyQR2 (gram, finish, apply, finish, apply) after the last
+    pass; A-check (pack, fused one-sided, sum) and the cross product
+    (gram, finish)."""
     passes = 2 * q + 1
-    compress = 2 + passes * 2 * prod + (passes - 1) * 3 + 5 + prod + 2
+    compress = 2 + passes * 3 + (passes - 1) * 3 + 5 + 3 + 2
     return compress + 1
 
 
@@ -194,7 +195,8 @@ TRAFFIC = {
 def _src_sha(kernel):
     import hashlib
     files = {"k_admm_fast": ["admm_fast.cuh", "admm_impl.cuh", "common.cuh"],
-             "k_tc_prod": ["tc.cu", "common.cuh"]}[kernel]
+             "k_tc_prod": ["tc.cu", "common.cuh"],
+             "k_fused_pass": ["fused.cu", "tc_ptx.cuh", "common.cuh"]}[kernel]
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_1505_04650_gb300", "csrc", f),
@@ -385,9 +387,10 @@ def main(argv=None):
         k: float(v) / 1e3 / iters for k, v in zip(names, ph.cpu().tolist())
         if k is not None}
 
-    # ---- the sketch products with A (one per side per pass), timed as a
-    # pass through the public call: B-panel packing + tensor-core product +
-    # split-tile fix-up, for A X and A^T Y
+    # ---- one power pass of the two-sided sketch (A X and A^T Y from one
+    # read of A), timed through the public call: panel pack + fused kernel
+    # + partial-slot sum.  Algorithmic bytes: one read of A, the two panels
+    # read and the two products written.
     X = torch.randn(n, d, device=dev)
     Y = torch.randn(m, d, device=dev)
     for _ in range(3):
@@ -401,9 +404,13 @@ def main(argv=None):
     e1.record(stream)
     torch.cuda.synchronize()
     pass_ms = e0.elapsed_time(e1) / reps          # A X and A^T Y
-    bytes_pass = 2 * (4.0 * m * n + 4.0 * (m + n) * d)
+    bytes_pass = 4.0 * m * n + 2 * 4.0 * (m + n) * d
     peaks = _peaks()
     sketch_gbs = bytes_pass / (pass_ms * 1e-3) / 1e9
+    # the whole compression: (2q + 2) reads of A (2q + 1 fused passes and
+    # A-check) over the compression's CUDA-event time
+    comp_bytes = (2 * q + 2) * 4.0 * m * n
+    comp_gbs = comp_bytes / (breakdown["compress_ms"] * 1e-3) / 1e9
 
     # ---- dominant kernel of the step: the compressed ADMM launch
     # (k_admm_fast, all 500 sweeps in one cooperative launch), timed by the
@@ -443,23 +450,36 @@ def main(argv=None):
         "roofline_sketch": {"bound": "hbm", "achieved": sketch_gbs,
                             "peak": peaks["hbm"], "unit": "GB/s",
                             "frac": sketch_gbs / peaks["hbm"],
-                            "traffic": _traffic("k_tc_prod", 1),
-                            "traffic_note": "product kernels only; pack "
-                                            "and fix-up read L2-resident "
-                                            "panels",
-                            "kernel": "cnmf_sketch_pass: k_pack_panel + "
-                                      "k_tc_prod (3xTF32 tcgen05) + "
-                                      "k_prod_fixup, A X and A^T Y",
+                            "traffic": _traffic("k_fused_pass", 1),
+                            "traffic_note": "the fused kernel's DRAM bytes "
+                                            "per pass (ncu); the pack and "
+                                            "the partial-slot sum read "
+                                            "L2-resident data",
+                            "kernel": "cnmf_sketch_pass: k_fu_pack + "
+                                      "k_fused_pass (one read of A, tcgen05 "
+                                      "bf16 hi+lo split) + k_fu_reduce",
                             "algorithmic_bytes": bytes_pass,
-                            "ms_per_pass": pass_ms},
+                            "algorithmic_bytes_note": "one read of A (4 m n) "
+                                                      "+ panels read and "
+                                                      "products written "
+                                                      "(8 (m + n) d)",
+                            "ms_per_pass": pass_ms,
+                            "compression": {
+                                "reads_of_A": 2 * q + 2,
+                                "algorithmic_bytes": comp_bytes,
+                                "ms": breakdown["compress_ms"],
+                                "achieved": comp_gbs,
+                                "frac": comp_gbs / peaks["hbm"],
+                                "note": "whole cnmf_compress incl. "
+                                        "CholeskyQR sweeps and A-tilde"}},
         "clocks": clk.summary(),
         "breakdown": breakdown,
         "gpu_launches": launches_per_step(q) * args.steps,
         "gpu_launches_note": "library kernels per step: 2 Gaussian panels, "
-                             "per pass 2 x (pack, product, fix-up) + one "
-                             "CholeskyQR sweep (gram, finish, apply), "
+                             "per pass (pack, fused pass, partial sum) + "
+                             "one CholeskyQR sweep (gram, finish, apply), "
                              "CholeskyQR2 after the last pass (5), A-check "
-                             "product, cross product (2), one ADMM launch",
+                             "(3), cross product (2), one ADMM launch",
     }
 
     # ---- end to end through the public API with host buffers: every step
@@ -621,19 +641,27 @@ def mixed_bench(cn, dev):
     import torch
     m = n = 50000
     r, d, q = 64, 80, 4
-    out = {"workload": "lowrank 50000 x 50000, r=64, d=80, q=4"}
+    out = {"workload": "lowrank 50000 x 50000, r=64, d=80, q=4 (and the "
+                       "same matrices with r=20, d=30: the fused pass)"}
     for name, dt in (("bf16", torch.bfloat16), ("fp32", torch.float32)):
         A = synth.lowrank_torch(m, n, r, 0.01, 1003, device=dev).to(dt)
         st = torch.zeros(1, dtype=torch.int32, device=dev)
-        ws = torch.empty(cn.lib().cnmf_compress_workspace(
-            m, n, d, 2 if name == "bf16" else 1), dtype=torch.uint8, device=dev)
-        ms = _time(lambda: cn.cnmf_compress(A, r, d, q, 2003, status=st, ws=ws),
-                   3, torch.cuda.current_stream(dev))
-        cn.raise_on_status(st, "mixed bench")
-        reads = 2 * (2 * q + 1) + 1
-        out[name] = {"compress_ms": ms,
-                     "gbs": reads * A.element_size() * m * n / (ms * 1e-3) / 1e9}
-        del A, ws
+        for rr, dd, key in ((r, d, name), (20, 30, name + "_d30")):
+            ws = torch.empty(cn.lib().cnmf_compress_workspace(
+                m, n, dd, 2 if name == "bf16" else 1), dtype=torch.uint8,
+                device=dev)
+            ms = _time(lambda: cn.cnmf_compress(A, rr, dd, q, 2003, status=st,
+                                                ws=ws),
+                       3, torch.cuda.current_stream(dev))
+            cn.raise_on_status(st, "mixed bench")
+            # d <= 32: the fused pass (2q + 1 passes and A-check, one read
+            # each); wider panels: one read per product
+            reads = 2 * q + 2 if dd <= 32 else 2 * (2 * q + 1) + 1
+            gbs = reads * A.element_size() * m * n / (ms * 1e-3) / 1e9
+            out[key] = {"d": dd, "compress_ms": ms, "reads_of_A": reads,
+                        "gbs": gbs, "frac": gbs / _peaks()["hbm"]}
+            del ws
+        del A
         torch.cuda.empty_cache()
     return out
 
