@@ -266,8 +266,10 @@ cnmf_status cnmf_factor(const void* L, const void* Rt, const void* Atilde,
  *           cnmf_batch_scratch_bytes(r, d) bytes kept between launches.
  *           flags & CNMF_BATCH_FRESH: start from U, V as given (Alg. 4
  *           setup: Yt = V R^T, Lam = Phi = 0); clear it for later launches.
- *           lambda <= 0 selects the balanced default lambda = phi =
- *           ||Atilde||_F / r, formed on the device from the item's Atilde.
+ *           lambda <= 0 selects the balanced scale lambda = phi =
+ *           c ||Atilde||_F / r, formed on the device from the item's
+ *           Atilde, with c = 1 for lambda = 0 and c = -lambda for
+ *           lambda < 0.
  *   max_r, max_d  bounds on the items' r and d (r <= 32, d <= 64, r <= d);
  *           they select the kernel variant and its shared-memory size.
  * The launch reads `items` when it runs, so a CUDA graph that captured it

@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(AD_NT)
   if (!(it.lambda > 0)) {
     // the balanced default lambda = phi = ||Atilde||_F / r, formed here
     // (FP64 squares, added in a fixed order) so the caller needs no host
-    // round trip after the compression
+    // round trip after the compression; a negative lambda scales it by
+    // -lambda
     __shared__ double nrm_s[AD_NT / 32 + 1];
     double s = 0.0;
     for (int e = threadIdx.x; e < d * d; e += AD_NT) {
@@ -100,7 +101,8 @@ __global__ void __launch_bounds__(AD_NT)
       nrm_s[AD_NT / 32] = sqrt(t) / r;
     }
     __syncthreads();
-    a.lam = a.phi = (W)nrm_s[AD_NT / 32];
+    const double scale = it.lambda < 0 ? -it.lambda : 1.0;
+    a.lam = a.phi = (W)(nrm_s[AD_NT / 32] * scale);
   }
 
   // cluster-wide sum of the shares in `buf` (entries [0, E)) in rank order

@@ -16,9 +16,17 @@ server
   one batched launch per cluster size (cnmf_factor_batched, replayed from a
   captured CUDA graph) advances every running request by `sweeps_per_round`
   sweeps; requests join at the next round after their compression and leave
-  when their sweep count is reached (iteration-level continuous batching);
-* on completion computes the relative residual (cnmf_residual) and frees
-  the request's memory.
+  when they are done (iteration-level continuous batching);
+* "done" is either a fixed sweep count (`iters`) or, with
+  `stop_at_target`, the accuracy target: the relative residual
+  rho = ||A - U V||_F / ||A||_F at or below tau = rho* + 1e-3, where rho*
+  is the residual of the rank-r truncation of the request's compressed
+  matrix lifted back to m x n (formed when the request joins).  rho is
+  computed (cnmf_residual) every `check_every` sweeps between rounds; a
+  request that reaches `max_sweeps` first leaves too and is counted as not
+  at target;
+* on completion keeps the relative residual and frees the request's
+  memory.
 
 Each request's arithmetic is independent of the others (batched kernel
 property), so its result is the same whether it is served alone or in a
@@ -61,6 +69,9 @@ class Request:
     cluster_size: int = 1
     rho: float = math.nan
     floor: float = math.nan
+    tau: float = math.nan        # accuracy target (stop_at_target)
+    At_host: torch.Tensor | None = None    # A-tilde copied to pinned memory
+    floor_res: torch.Tensor | None = None  # residual of the truncation
     nbytes: int = 0
     done_sweeps: int = 0
     problem: BatchProblem | None = None
@@ -97,7 +108,7 @@ def truncation_factors(L: torch.Tensor, Rt: torch.Tensor, Atilde: torch.Tensor,
     of the compressed matrix: m x r and n x r FP32 factors.  The residual
     ||A - F G^T|| is the best rank-r fit the sketch can express -- computed
     as a residual, not as ||A||^2 - sum sigma_i^2, which cancels
-    catastrophically when the floor is small."""
+    catastrophically when the floor is small.  Atilde may be a host copy."""
     U, s, Vh = torch.linalg.svd(Atilde.double().cpu())
     Us = (U[:, :r] * s[:r]).to(L.device)
     V = Vh[:r].T.contiguous().to(L.device)
@@ -120,8 +131,20 @@ class Server:
     def __init__(self, hbm_budget: float = 40e9, max_slots: int = 512,
                  sweeps_per_round: int = 10, compress_streams: int = 4,
                  tuner: Autotuner | None = None, use_graphs: bool = True,
+                 stop_at_target: bool = False, check_every: int = 20,
+                 max_sweeps: int = 3000, penalty_scale: float = 0.3,
                  device="cuda"):
         self.dev = torch.device(device)
+        self.stop_at_target = stop_at_target
+        # residual checks fall on round boundaries
+        self.check_every = max(sweeps_per_round,
+                               check_every // sweeps_per_round * sweeps_per_round)
+        self.max_sweeps = max_sweeps
+        # lambda = phi = penalty_scale ||Atilde||_F / r, formed by the
+        # batched kernel from each request's A-tilde.  Alg. 4 leaves the
+        # penalties open; on this request mix 0.3 reached the accuracy
+        # target in every sampled request (1.0 stalled above it in several)
+        self.penalty_scale = penalty_scale
         self.budget = int(hbm_budget)
         self.max_slots = max_slots
         self.S = sweeps_per_round
@@ -223,6 +246,13 @@ class Server:
                                              rq.seed + 2, status=self.status,
                                              ws=ws)
                 rq.problem = BatchProblem(L, Rt, At, U0, Vt0, 1.0, 1.0)
+                if self.stop_at_target:
+                    # A-tilde to the host for the target (an asynchronous
+                    # copy: nothing here may synchronise while the main
+                    # thread captures a graph)
+                    rq.At_host = torch.empty(At.shape, dtype=At.dtype,
+                                             pin_memory=True)
+                    rq.At_host.copy_(At, non_blocking=True)
                 rq.event = torch.cuda.Event()
                 rq.event.record(s)
         finally:
@@ -230,19 +260,28 @@ class Server:
         rq.cluster_size = self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
 
     def _ready(self, rq: Request, now: float):
-        # penalty: lambda = phi = ||Atilde||_F / r, formed by the batched
-        # kernel itself (lambda <= 0), so nothing waits for the device here
+        # penalty: lambda = phi = penalty_scale ||Atilde||_F / r, formed by
+        # the batched kernel itself (a negative lambda is that scale), so
+        # nothing waits for the device here
         pb = rq.problem
-        pb.lam = pb.phi = 0.0
+        pb.lam = pb.phi = -self.penalty_scale
         for t in (pb.L, pb.Rt, pb.Atilde, pb.U, pb.Vt, pb.state.buf,
                   pb.scratch, rq.A):
             t.record_stream(self.main)
         rq.t_compressed = now
+        if self.stop_at_target:
+            # the target's reference point, the residual of the rank-r
+            # truncation of A-tilde (host SVD of the d x d copy), queued on
+            # the main stream and read after the next round
+            rq.floor_res = cnmf_residual(
+                rq.A, *truncation_factors(pb.L, pb.Rt, rq.At_host, rq.r))
 
-    def _finish(self, rq: Request, res: torch.Tensor, res_floor: torch.Tensor):
+    def _finish(self, rq: Request, res: torch.Tensor,
+                res_floor: torch.Tensor | None):
         e2, a2 = float(res[0]), float(res[1])
         rq.rho = math.sqrt(e2 / a2)
-        rq.floor = math.sqrt(float(res_floor[0]) / a2)
+        if res_floor is not None:
+            rq.floor = math.sqrt(float(res_floor[0]) / a2)
         if rq.keep:
             rq.U = rq.problem.U.clone()
             rq.Vt = rq.problem.Vt.clone()
@@ -296,6 +335,36 @@ class Server:
                     for i in range(0, len(reqs), self.max_slots):
                         self._round(key, reqs[i:i + self.max_slots])
                 rounds += 1
+                if self.stop_at_target:
+                    # residual of the requests due for a check
+                    due = [rq for rq in running
+                           if rq.done_sweeps % self.check_every == 0
+                           or rq.done_sweeps >= self.max_sweeps]
+                    outs = [cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt)
+                            for rq in due]
+                    self.main.synchronize()   # this round only
+                    now = clock()
+                    for rq in running:
+                        if rq.floor_res is not None:
+                            e2, a2 = rq.floor_res.cpu().tolist()
+                            rq.floor = math.sqrt(e2 / a2)
+                            rq.tau = rq.floor + 1e-3
+                            rq.floor_res = None
+                    finished = []
+                    for rq, res in zip(due, outs):
+                        res = res.cpu()
+                        e2, a2 = res.tolist()
+                        if math.sqrt(e2 / a2) <= rq.tau or \
+                                rq.done_sweeps >= self.max_sweeps:
+                            rq.t_done = now
+                            self._finish(rq, res, None)
+                            finished.append(rq)
+                    gone = set(id(rq) for rq in finished)
+                    running = [rq for rq in running if id(rq) not in gone]
+                    for rq in finished:
+                        in_use -= rq.nbytes
+                        done.append(rq)
+                    continue
                 finished = [rq for rq in running if rq.done_sweeps >= rq.iters]
                 running = [rq for rq in running if rq.done_sweeps < rq.iters]
                 outs = []
@@ -324,14 +393,25 @@ class Server:
         wall = clock()
         lat = np.array([rq.t_done - rq.t_arrive for rq in done]) * 1e3
         ok = np.array([rq.rho <= rq.floor + 1e-3 for rq in done])
-        return {
+        sweeps = np.array([rq.done_sweeps for rq in done])
+        out = {
             "requests": total, "wall_s": wall,
             "factorizations_per_s": total / wall,
             "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()),
             "frac_at_target": float(ok.mean()),
+            "sweeps_mean": float(sweeps.mean()),
+            "sweeps_p99": float(np.percentile(sweeps, 99)),
+            "stop": ("rho <= rho* + 1e-3, checked every "
+                     f"{self.check_every} sweeps, cap {self.max_sweeps}"
+                     if self.stop_at_target else "fixed sweep count"),
+            "penalty": f"lambda = phi = {self.penalty_scale} ||Atilde||_F / r",
             "rounds": rounds, "sweeps_per_round": self.S,
             "cluster_sizes": {str(c): int(sum(rq.cluster_size == c for rq in done))
                               for c in (1, 2, 4, 8)},
         }
+        if ok.any():
+            out["p50_at_target_ms"] = float(np.percentile(lat[ok], 50))
+            out["p99_at_target_ms"] = float(np.percentile(lat[ok], 99))
+        return out
