@@ -397,6 +397,31 @@ cnmf_status cnmf_factor_als(const void* A, cnmf_dtype a_type, int64_t m,
                             cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_factor_mu: compressed alternating NMF (Alg. 2, Sec. III) with the
+ * multiplicative updates of Ding, Li & Jordan (2010, Eq. 8) -- the paper's
+ * other inner solver -- in their semi-NMF form (A-check and A-hat have
+ * entries of both signs).  With B+ = (|B| + B) / 2, B- = (|B| - B) / 2,
+ * `iters` times:
+ *   Y-check = Y R^T;  P = A-check Y-check^T, Q = Y-check Y-check^T,
+ *     X <- X * sqrt((P+ + X Q-) / (P- + X Q+))             (entrywise)
+ *   X-hat = L^T X;    P = A-hat^T X-hat, Q = X-hat^T X-hat,
+ *     Y^T <- Y^T * sqrt((P+ + Y^T Q-) / (P- + Y^T Q+))
+ * a zero denominator floored at 1e-300 (FP64) / 1e-38 (FP32); an entry
+ * that is zero stays zero.
+ *   A, L, Rt, r, d as in cnmf_factor_als (same workspace query).
+ *   X  in/out, m x r (the start X0 on entry);  Y  in/out, r x n.
+ *   dev_status: CNMF_E_NONFINITE if an update is not finite.
+ * ---------------------------------------------------------------------- */
+size_t cnmf_factor_mu_workspace(int64_t m, int64_t n, int32_t r, int32_t d,
+                                cnmf_dtype a_type);
+cnmf_status cnmf_factor_mu(const void* A, cnmf_dtype a_type, int64_t m,
+                           int64_t n, int64_t lda, const void* L,
+                           const void* Rt, int32_t r, int32_t d,
+                           int32_t iters, void* X, void* Y, void* ws,
+                           size_t ws_bytes, int32_t* dev_status,
+                           cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_residual: out2[0] = ||A - U V||_F^2, out2[1] = ||A||_F^2 (FP64,
  * device), in one read of A (Sec. V reports sqrt(out2[0] / out2[1])).
  *   U m x r, Vt n x r in w_type (CNMF_F64 or CNMF_F32), 1 <= r <= 128.

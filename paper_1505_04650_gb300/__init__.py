@@ -27,7 +27,7 @@ __all__ = [
     "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
     "sketch_size", "default_penalty", "BatchProblem", "cnmf_factor_batched",
     "set_thread_cta_limit", "snmf_right_factor", "cnmf_compress_gaussian",
-    "cnmf_factor_als",
+    "cnmf_factor_als", "cnmf_factor_mu",
 ]
 
 
@@ -407,6 +407,34 @@ def cnmf_factor_als(A: torch.Tensor, L: torch.Tensor, Rt: torch.Tensor,
                               _ptr(Y), _ptr(unconv), _ptr(ws), ws.numel(),
                               _ptr(st), _stream(dev)), "cnmf_factor_als")
     return X, Y, unconv, st
+
+
+def cnmf_factor_mu(A: torch.Tensor, L: torch.Tensor, Rt: torch.Tensor,
+                   X0: torch.Tensor, Y0: torch.Tensor, iters: int,
+                   status: torch.Tensor | None = None, ws=None):
+    """Alg. 2 with multiplicative-update steps -> (X m x r, Y r x n,
+    status); X0 (m x r) and Y0 (r x n) are the start (copied)."""
+    m, n, lda = _mat(A)
+    w = _wdtype(A.dtype)
+    d = L.shape[1]
+    r = Y0.shape[0]
+    _dense(L, (m, d), w, "L")
+    _dense(Rt, (n, d), w, "Rt")
+    _dense(X0, (m, r), w, "X0")
+    _dense(Y0, (r, n), w, "Y0")
+    dev = A.device
+    X = X0.clone()
+    Y = Y0.clone()
+    st = status if status is not None else _status(dev)
+    lb = lib()
+    nb = lb.cnmf_factor_mu_workspace(m, n, r, d, _DT[A.dtype])
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(lb.cnmf_factor_mu(_ptr(A), _DT[A.dtype], m, n, lda, _ptr(L),
+                             _ptr(Rt), r, d, iters, _ptr(X), _ptr(Y),
+                             _ptr(ws), ws.numel(), _ptr(st), _stream(dev)),
+           "cnmf_factor_mu")
+    return X, Y, st
 
 
 def cnmf_residual(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,

@@ -94,6 +94,12 @@ SIGNATURES = {
                                   c_int32, c_int32, c_double, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_size_t,
                                   c_void_p, c_void_p]),
+    "cnmf_factor_mu_workspace": (c_size_t, [c_int64, c_int64, c_int32,
+                                            c_int32, c_int32]),
+    "cnmf_factor_mu": (c_int32, [c_void_p, c_int32, c_int64, c_int64, c_int64,
+                                 c_void_p, c_void_p, c_int32, c_int32, c_int32,
+                                 c_void_p, c_void_p, c_void_p, c_size_t,
+                                 c_void_p, c_void_p]),
     "snmf_right_factor_workspace": (c_size_t, [c_int64, c_int32, c_int32,
                                                c_int32]),
     "snmf_right_factor": (c_int32, [c_void_p, c_int32, c_int64, c_int32,

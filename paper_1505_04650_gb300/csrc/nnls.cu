@@ -22,6 +22,15 @@
 // against Y-check^T, and the Y step, for every column of A-hat, against
 // X-hat.
 //
+// The other inner solver of Alg. 2 is the semi-NMF multiplicative update of
+// Ding, Li & Jordan (2010, Eq. 8; the compressed matrices have both signs):
+// for min_{X >= 0} ||M - X F|| (F: r x d) with P = M F^T, Q = F F^T and the
+// positive / negative parts B+ = (|B| + B) / 2, B- = (|B| - B) / 2,
+//   X <- X * sqrt((P+ + X Q-) / (P- + X Q+))   entrywise,
+// a zero denominator floored at 1e-300 (a reading: the paper and Ding et
+// al. leave it open).  k_mu_step does one such update for every row, one
+// row per thread, with F and Q in shared memory.
+//
 // Launches: (1) one CTA gathers B from the rows K of Rhat^T and forms G and
 // G^-1 (Gauss-Jordan in FP64);
 // (2) the library's product kernel forms Bt = Rhat^T B (n x r, = b_i^T by
@@ -351,6 +360,12 @@ static AlsLayout als_layout(void* ws, int64_t m, int64_t n, int r, int d,
 }
 
 template <typename W>
+static cnmf_status als_inputs(const void* A, cnmf_dtype a_type, int64_t m,
+                              int64_t n, int64_t lda, const W* Lm,
+                              const W* Rt, int d, const AlsLayout& L,
+                              int32_t* status, cudaStream_t s);
+
+template <typename W>
 static cnmf_status als_run(const void* A, cnmf_dtype a_type, int64_t m,
                            int64_t n, int64_t lda, const W* Lm, const W* Rt,
                            int r, int d, int iters, int max_sweeps,
@@ -362,11 +377,8 @@ static cnmf_status als_run(const void* A, cnmf_dtype a_type, int64_t m,
   W* aht = (W*)L.aht;
   W* yc = (W*)L.yc;
   W* xh = (W*)L.xh;
-  // A-check = A R^T (m x d), A-hat^T = A^T L (n x d): one read of A each
-  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, ach, d, d, status};
-  CNMF_TRY(launch_prod(pc, L.prod_ws, L.prod_bytes, s));
-  ProdArgs ph{A, a_type, m, n, lda, true, Lm, d, d, aht, d, d, status};
-  CNMF_TRY(launch_prod(ph, L.prod_ws, L.prod_bytes, s));
+  // A-check = A R^T (m x d), A-hat^T = A^T L (n x d)
+  CNMF_TRY(als_inputs<W>(A, a_type, m, n, lda, Lm, Rt, d, L, status, s));
   for (int it = 0; it < iters; ++it) {
     // Y-check = Y R^T (r x d)
     ProdArgs py{Y, w, r, n, n, false, Rt, d, d, yc, d, d, status};
@@ -382,6 +394,140 @@ static cnmf_status als_run(const void* A, cnmf_dtype a_type, int64_t m,
     CNMF_TRY(nnls_run<W>(aht, d, n, d, nullptr, 0, 0, nullptr, xh, r, 1, r,
                          max_sweeps, tol, Y, n, 1, unconverged, L.nn, status,
                          s));
+  }
+  return CNMF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Multiplicative update (Alg. 2 inner solver, Ding et al. Eq. 8): for every
+// row i of M (rows x d, pitch ldm), x = X[i, :] (x_k at X[i si + k sk]),
+//   p = M[i] F^T,  x_k <- x_k sqrt((p+_k + (x Q-)_k) / max(p-_k + (x Q+)_k,
+//   1e-300)),  Q = F F^T,
+// F (r x d) read as F[k][c] = Fs[k fk + c fc].  Every block forms F and Q
+// in shared memory (r^2 d multiply-adds, in a fixed order, so every row
+// sees the same Q).  A non-finite result sets CNMF_E_NONFINITE.
+// ---------------------------------------------------------------------------
+constexpr int MU_NT = 128;
+
+template <typename W, int RMAX>
+__global__ void __launch_bounds__(MU_NT)
+    k_mu_step(const W* __restrict__ M, int64_t ldm, int64_t rows, int d,
+              const W* __restrict__ Fs, int64_t fk, int64_t fc, int r,
+              W* __restrict__ X, int64_t si, int64_t sk,
+              int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* F = reinterpret_cast<W*>(smem_raw);    // RMAX x d
+  W* Q = F + (size_t)RMAX * d;              // RMAX x RMAX
+  for (int e = threadIdx.x; e < r * d; e += MU_NT) {
+    const int k = e / d, c = e - k * d;
+    F[k * d + c] = Fs[k * fk + c * fc];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += MU_NT) {
+    const int k = e / r, l = e - k * r;
+    W q = W(0);
+    for (int c = 0; c < d; ++c) q = fma(F[k * d + c], F[l * d + c], q);
+    Q[k * RMAX + l] = q;
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * MU_NT + threadIdx.x;
+  if (i >= rows) return;
+  W p[RMAX], x[RMAX];
+#pragma unroll
+  for (int k = 0; k < RMAX; ++k) {
+    p[k] = W(0);
+    x[k] = k < r ? X[i * si + k * sk] : W(0);
+  }
+  const W* mi = M + i * ldm;
+  for (int c = 0; c < d; ++c) {
+    const W v = mi[c];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k)
+      if (k < r) p[k] = fma(v, F[k * d + c], p[k]);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < RMAX; ++k) {
+    if (k >= r) break;
+    W num = p[k] > W(0) ? p[k] : W(0);
+    W den = p[k] < W(0) ? -p[k] : W(0);
+    for (int l = 0; l < r; ++l) {
+      const W q = Q[l * RMAX + k];
+      if (q < W(0)) num = fma(x[l], -q, num);
+      else den = fma(x[l], q, den);
+    }
+    const W floor_den = sizeof(W) == 8 ? W(1e-300) : W(1e-38);
+    const W xn = x[k] * sqrt(num / (den > floor_den ? den : floor_den));
+    bad |= !isfinite((double)xn);
+    X[i * si + k * sk] = xn;
+  }
+  if (bad) set_status(status, CNMF_E_NONFINITE);
+}
+
+template <typename W>
+static cnmf_status mu_launch(const W* M, int64_t ldm, int64_t rows, int d,
+                             const W* Fs, int64_t fk, int64_t fc, int r, W* X,
+                             int64_t si, int64_t sk, int32_t* status,
+                             cudaStream_t s) {
+  const unsigned grid = (unsigned)ceil_div(rows, MU_NT);
+#define MU_CASE(RM)                                                          \
+  {                                                                          \
+    const size_t smem = sizeof(W) * ((size_t)RM * d + (size_t)RM * RM);      \
+    if (!ensure_max_smem((const void*)k_mu_step<W, RM>, smem))               \
+      return CNMF_E_INVALID_ARG;                                             \
+    k_mu_step<W, RM><<<grid, MU_NT, smem, s>>>(M, ldm, rows, d, Fs, fk, fc,  \
+                                               r, X, si, sk, status);        \
+    CNMF_CHECK_LAUNCH();                                                     \
+    return CNMF_OK;                                                          \
+  }
+  if (r <= 16) MU_CASE(16)
+  if (r <= 32) MU_CASE(32)
+  MU_CASE(64)
+#undef MU_CASE
+}
+
+// A-check = A R^T (m x d) and A-hat^T = A^T L (n x d): one fused read of A
+// where the fused pass applies, else one read per product.
+template <typename W>
+static cnmf_status als_inputs(const void* A, cnmf_dtype a_type, int64_t m,
+                              int64_t n, int64_t lda, const W* Lm,
+                              const W* Rt, int d, const AlsLayout& L,
+                              int32_t* status, cudaStream_t s) {
+  if (fused_applicable(A, a_type, m, n, lda, d)) {
+    FusedArgs fa{A, a_type, m, n, lda, Rt, d, Lm, d, d, L.ach, d, L.aht, d,
+                 status};
+    return launch_fused(fa, L.prod_ws, L.prod_bytes, s);
+  }
+  ProdArgs pc{A, a_type, m, n, lda, false, Rt, d, d, L.ach, d, d, status};
+  CNMF_TRY(launch_prod(pc, L.prod_ws, L.prod_bytes, s));
+  ProdArgs ph{A, a_type, m, n, lda, true, Lm, d, d, L.aht, d, d, status};
+  return launch_prod(ph, L.prod_ws, L.prod_bytes, s);
+}
+
+template <typename W>
+static cnmf_status mu_run(const void* A, cnmf_dtype a_type, int64_t m,
+                          int64_t n, int64_t lda, const W* Lm, const W* Rt,
+                          int r, int d, int iters, W* X, W* Y,
+                          const AlsLayout& L, int32_t* status,
+                          cudaStream_t s) {
+  const cnmf_dtype w = sizeof(W) == 8 ? CNMF_F64 : CNMF_F32;
+  W* ach = (W*)L.ach;
+  W* aht = (W*)L.aht;
+  W* yc = (W*)L.yc;
+  W* xh = (W*)L.xh;
+  CNMF_TRY(als_inputs<W>(A, a_type, m, n, lda, Lm, Rt, d, L, status, s));
+  for (int it = 0; it < iters; ++it) {
+    // Y-check = Y R^T (r x d)
+    ProdArgs py{Y, w, r, n, n, false, Rt, d, d, yc, d, d, status};
+    CNMF_TRY(launch_prod(py, L.prod_ws, L.prod_bytes, s));
+    // X step: M = A-check, F = Y-check; X row i at X[i r + k]
+    CNMF_TRY(mu_launch<W>(ach, d, m, d, yc, d, 1, r, X, r, 1, status, s));
+    // X-hat = L^T X (d x r)
+    ProdArgs px{Lm, w, m, d, d, true, X, r, r, xh, r, r, status};
+    CNMF_TRY(launch_prod(px, L.prod_ws, L.prod_bytes, s));
+    // Y step (transposed): M = A-hat^T, F = X-hat^T (F[k][c] = xh[c r + k]),
+    // row j of Y^T = column j of Y (Y[k n + j])
+    CNMF_TRY(mu_launch<W>(aht, d, n, d, xh, 1, r, r, Y, 1, n, status, s));
   }
   return CNMF_OK;
 }
@@ -455,4 +601,33 @@ extern "C" cnmf_status cnmf_factor_als(const void* A, cnmf_dtype a_type,
   return als_run<float>(A, a_type, m, n, lda, (const float*)L,
                         (const float*)Rt, r, d, iters, max_sweeps, tol,
                         (float*)X, (float*)Y, unconverged, lay, dev_status, s);
+}
+
+extern "C" size_t cnmf_factor_mu_workspace(int64_t m, int64_t n, int32_t r,
+                                           int32_t d, cnmf_dtype a_type) {
+  return cnmf_factor_als_workspace(m, n, r, d, a_type);
+}
+
+extern "C" cnmf_status cnmf_factor_mu(const void* A, cnmf_dtype a_type,
+                                      int64_t m, int64_t n, int64_t lda,
+                                      const void* L, const void* Rt, int32_t r,
+                                      int32_t d, int32_t iters, void* X,
+                                      void* Y, void* ws, size_t ws_bytes,
+                                      int32_t* dev_status,
+                                      cnmf_stream_t stream) {
+  if ((a_type != CNMF_F64 && a_type != CNMF_F32 && a_type != CNMF_BF16) ||
+      !A || !L || !Rt || !X || !Y || !ws || m < 1 || n < 1 || lda < n ||
+      d < 1 || d > 128 || d > m || d > n || r < 1 || r > 64 || r > d ||
+      iters < 0)
+    return CNMF_E_INVALID_ARG;
+  AlsLayout lay = als_layout(ws, m, n, r, d, a_type);
+  if (ws_bytes < lay.bytes) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a_type == CNMF_F64)
+    return mu_run<double>(A, a_type, m, n, lda, (const double*)L,
+                          (const double*)Rt, r, d, iters, (double*)X,
+                          (double*)Y, lay, dev_status, s);
+  return mu_run<float>(A, a_type, m, n, lda, (const float*)L,
+                       (const float*)Rt, r, d, iters, (float*)X, (float*)Y,
+                       lay, dev_status, s);
 }

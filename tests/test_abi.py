@@ -138,6 +138,22 @@ def test_als_and_gaussian_compression_invalid_arguments(lib):
     assert als(sweeps=0) == E
     assert als(tol=-1.0) == E
     assert lib.cnmf_factor_als_workspace(100, 80, 11, 10, 1) == 0
+    # cnmf_factor_mu(A, a_type, m, n, lda, L, Rt, r, d, iters, X, Y, ws,
+    #                ws_bytes, status, stream)
+    def mu(**kw):
+        a = dict(m=100, n=80, lda=80, r=4, d=10, iters=2)
+        a.update(kw)
+        return lib.cnmf_factor_mu(f, 1, a["m"], a["n"], a["lda"], f, f, a["r"],
+                                  a["d"], a["iters"], f, f, f, 1 << 30, None,
+                                  None)
+    assert mu(r=11) == E
+    assert mu(d=81, r=4) == E
+    assert mu(lda=79) == E
+    assert mu(iters=-1) == E
+    assert mu(r=65, d=70) == E
+    assert lib.cnmf_factor_mu_workspace(100, 80, 11, 10, 1) == 0
+    assert lib.cnmf_factor_mu_workspace(100, 80, 4, 10, 1) == \
+        lib.cnmf_factor_als_workspace(100, 80, 4, 10, 1)
     # cnmf_compress_gaussian(A, a_type, m, n, lda, d, seed, L, Rt, Atilde,
     #                        ws, ws_bytes, status, stream)
     assert lib.cnmf_compress_gaussian(f, 1, 100, 80, 80, 0, 1, f, f, f, f,
