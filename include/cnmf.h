@@ -198,6 +198,37 @@ cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type, int64_t m,
                           cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_compress_host: cnmf_compress for an A that does not stay in device
+ * memory -- the paper's out-of-core setting (Sec. II, big-data solutions;
+ * App. A): A in host memory is streamed through the GPU once per pass.
+ *   A           m x n, pitch lda, in memory the copy engine reads (host
+ *               memory: page-locked for the full copy rate, pageable works
+ *               slower; a device pointer works too).  It must stay valid
+ *               and unchanged until the stream has finished the call.
+ *   block_rows  rows per block (>= 1): each block is copied into one
+ *               device buffer of block_rows x n and goes through the same
+ *               product kernels as cnmf_compress (the fused one-read pass
+ *               for FP32 / BF16 and d <= 32); the blocks' shares of A^T Y
+ *               are added in block order.
+ *   Everything else as cnmf_compress: the m x d and n x d panels, their
+ *   CholeskyQR2 (whose Gram matrices are the sums over row blocks -- the
+ *   one central reduction TSQR provides in the paper) and A-tilde stay in
+ *   device memory, of which the call needs the workspace below plus L, Rt,
+ *   Atilde (O((m + n) d) and block_rows x n, not m x n).  A is read from
+ *   host memory 2q + 2 times (d <= 32, FP32/BF16) or 4q + 3 times.
+ *   Results equal cnmf_compress's up to the order of FP32 additions.
+ * ---------------------------------------------------------------------- */
+size_t cnmf_compress_host_workspace(int64_t m, int64_t n, int32_t d,
+                                    cnmf_dtype a_type, int64_t block_rows);
+cnmf_status cnmf_compress_host(const void* A, cnmf_dtype a_type, int64_t m,
+                               int64_t n, int64_t lda, int32_t r, int32_t d,
+                               int32_t q, uint64_t seed, const void* Omega,
+                               const void* Psi, void* L, void* Rt,
+                               void* Atilde, int64_t block_rows, void* ws,
+                               size_t ws_bytes, int32_t* dev_status,
+                               cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_compress_gaussian: the Gaussian-compression baseline the paper
  * compares against (Sec. II, note on data-agnostic compression: Q =
  * s^-1/2 Omega), applied on both sides with s = d and no power iteration or

@@ -27,7 +27,7 @@ __all__ = [
     "cnmf_factor_plain", "snmf_select", "cnmf_residual", "FactorState",
     "sketch_size", "default_penalty", "BatchProblem", "cnmf_factor_batched",
     "set_thread_cta_limit", "snmf_right_factor", "cnmf_compress_gaussian",
-    "cnmf_factor_als", "cnmf_factor_mu",
+    "cnmf_factor_als", "cnmf_factor_mu", "cnmf_compress_host",
 ]
 
 
@@ -192,6 +192,42 @@ def cnmf_compress(A: torch.Tensor, r: int, d: int, q: int, seed: int,
                            _ptr(Omega), _ptr(Psi), _ptr(Lm), _ptr(Rt),
                            _ptr(At), _ptr(ws), ws.numel(), _ptr(st),
                            _stream(dev)), "cnmf_compress")
+    return Lm, Rt, At, st
+
+
+def cnmf_compress_host(A: torch.Tensor, r: int, d: int, q: int, seed: int,
+                       block_rows: int, device="cuda",
+                       Omega: torch.Tensor | None = None,
+                       Psi: torch.Tensor | None = None,
+                       status: torch.Tensor | None = None, ws=None):
+    """Two-sided compression of an A that stays outside device memory (a
+    CPU tensor, ideally pinned; a CUDA tensor is accepted too), streamed
+    through the GPU in blocks of `block_rows` rows -> (L, Rt, Atilde,
+    status) on `device`."""
+    if A.dim() != 2 or A.dtype not in _DT or A.stride(1) != 1 or \
+            A.stride(0) < A.shape[1]:
+        raise ValueError("A must be a 2-D row-major float64/float32/bfloat16 "
+                         "tensor with unit column stride")
+    m, n, lda = A.shape[0], A.shape[1], A.stride(0)
+    dev = torch.device(device)
+    w = _wdtype(A.dtype)
+    if Omega is not None:
+        _dense(Omega, (n, d), w, "Omega")
+    if Psi is not None:
+        _dense(Psi, (m, d), w, "Psi")
+    Lm = torch.empty(m, d, dtype=w, device=dev)
+    Rt = torch.empty(n, d, dtype=w, device=dev)
+    At = torch.empty(d, d, dtype=w, device=dev)
+    st = status if status is not None else _status(dev)
+    L = lib()
+    nb = L.cnmf_compress_host_workspace(m, n, d, _DT[A.dtype], block_rows)
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(L.cnmf_compress_host(_ptr(A), _DT[A.dtype], m, n, lda, r, d, q,
+                                seed, _ptr(Omega), _ptr(Psi), _ptr(Lm),
+                                _ptr(Rt), _ptr(At), block_rows, _ptr(ws),
+                                ws.numel(), _ptr(st), _stream(dev)),
+           "cnmf_compress_host")
     return Lm, Rt, At, st
 
 

@@ -63,6 +63,13 @@ SIGNATURES = {
                                 c_int32, c_int32, c_int32, c_uint64, c_void_p,
                                 c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_size_t, c_void_p, c_void_p]),
+    "cnmf_compress_host_workspace": (c_size_t, [c_int64, c_int64, c_int32,
+                                                c_int32, c_int64]),
+    "cnmf_compress_host": (c_int32, [c_void_p, c_int32, c_int64, c_int64,
+                                     c_int64, c_int32, c_int32, c_int32,
+                                     c_uint64, c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_int64, c_void_p,
+                                     c_size_t, c_void_p, c_void_p]),
     "cnmf_factor_workspace": (c_size_t, [c_int64, c_int64, c_int32, c_int32,
                                          c_int32]),
     "cnmf_factor_state_bytes": (c_size_t, [c_int64, c_int64, c_int32, c_int32,

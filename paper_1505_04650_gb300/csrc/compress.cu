@@ -52,8 +52,11 @@ struct CompressLayout {
   size_t prod_bytes, orth_bytes;
 };
 
+// prod_rows: the row count of the matrices the product kernels see (m, or
+// the row-block size when A is streamed from host memory)
 static CompressLayout compress_layout(void* ws, int64_t m, int64_t n, int d,
-                                      cnmf_dtype a_type) {
+                                      cnmf_dtype a_type,
+                                      int64_t prod_rows = -1) {
   CompressLayout L;
   cnmf_dtype w = work_type(a_type);
   size_t e = wbytes(w);
@@ -66,7 +69,7 @@ static CompressLayout compress_layout(void* ws, int64_t m, int64_t n, int d,
   L.n0 = cv.take<char>((size_t)n * L.KP * e);
   L.n1 = cv.take<char>((size_t)n * L.KP * e);
   L.acheck = cv.take<char>((size_t)m * L.KP * e);
-  L.prod_bytes = prod_workspace(m, n, d, a_type);
+  L.prod_bytes = prod_workspace(prod_rows > 0 ? prod_rows : m, n, d, a_type);
   L.prod_ws = cv.take<char>(L.prod_bytes);
   L.orth_bytes = std::max(orth_workspace(std::max(m, n), d, w),
                           cross_workspace(m, d, w));
@@ -153,24 +156,175 @@ extern "C" size_t cnmf_compress_workspace(int64_t m, int64_t n, int32_t d,
   return compress_layout(nullptr, m, n, d, a_type).bytes;
 }
 
-extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
-                                     int64_t m, int64_t n, int64_t lda,
-                                     int32_t r, int32_t d, int32_t q,
-                                     uint64_t seed, const void* Omega,
-                                     const void* Psi, void* L, void* Rt,
-                                     void* Atilde, void* ws, size_t ws_bytes,
-                                     int32_t* dev_status,
-                                     cnmf_stream_t stream) {
-  if (!valid_type(a_type) || !A || !L || !Rt || !Atilde || !ws || m < 1 ||
-      n < 1 || lda < n || r < 1 || d < r || d > 128 || d > m || d > n ||
-      q < 0 || q > 64)
-    return CNMF_E_INVALID_ARG;
-  CompressLayout lay = compress_layout(ws, m, n, d, a_type);
-  if (ws_bytes < lay.bytes) return CNMF_E_WORKSPACE;
-  cudaStream_t s = (cudaStream_t)stream;
+namespace cnmf {
+
+// Where the passes over A come from: A resident in device memory, or A in
+// host memory streamed through the GPU in row blocks.
+struct PassSource {
+  // Zm = A X (m x KP panel) and Zn = A^T Y (n x KP panel)
+  virtual cnmf_status both(const void* X, int64_t ldx, const void* Y,
+                           int64_t ldy, void* zm, void* zn) = 0;
+  // Zm = A X only (A-check = A R^T)
+  virtual cnmf_status left(const void* X, int64_t ldx, void* zm) = 0;
+  virtual ~PassSource() = default;
+};
+
+// A in device memory: the fused pass (one read of A for both products)
+// where it applies, else one read per product.
+struct DeviceSource : PassSource {
+  const void* A;
+  cnmf_dtype a_type;
+  int64_t m, n, lda;
+  int d;
+  const CompressLayout* lay;
+  int32_t* status;
+  cudaStream_t s;
+  cnmf_status both(const void* X, int64_t ldx, const void* Y, int64_t ldy,
+                   void* zm, void* zn) override {
+    const int KP = lay->KP;
+    if (fused_applicable(A, a_type, m, n, lda, d)) {
+      FusedArgs fa{A, a_type, m, n, lda, X, ldx, Y, ldy, d, zm, KP, zn, KP,
+                   status};
+      return launch_fused(fa, lay->prod_ws, lay->prod_bytes, s);
+    }
+    ProdArgs pa{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d, status};
+    CNMF_TRY(launch_prod(pa, lay->prod_ws, lay->prod_bytes, s));
+    ProdArgs pt{A, a_type, m, n, lda, true, Y, ldy, d, zn, KP, d, status};
+    return launch_prod(pt, lay->prod_ws, lay->prod_bytes, s);
+  }
+  cnmf_status left(const void* X, int64_t ldx, void* zm) override {
+    const int KP = lay->KP;
+    if (fused_applicable(A, a_type, m, n, lda, d, true, false)) {
+      FusedArgs fa{A, a_type, m, n, lda, X, ldx, nullptr, 0, d, zm, KP,
+                   nullptr, 0, status};
+      return launch_fused(fa, lay->prod_ws, lay->prod_bytes, s);
+    }
+    ProdArgs pc{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d, status};
+    return launch_prod(pc, lay->prod_ws, lay->prod_bytes, s);
+  }
+};
+
+// x[i] = y[i] (first) or x[i] + y[i]
+template <typename W>
+__global__ void k_acc(W* __restrict__ x, const W* __restrict__ y,
+                      int64_t count, int first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = first ? y[i] : x[i] + y[i];
+}
+
+static cnmf_status launch_acc(void* x, const void* y, int64_t count,
+                              bool first, cnmf_dtype w, cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((count + 255) / 256, 4 * num_sms()));
+  if (w == CNMF_F64)
+    k_acc<double><<<grid, 256, 0, s>>>((double*)x, (const double*)y, count,
+                                       first ? 1 : 0);
+  else
+    k_acc<float><<<grid, 256, 0, s>>>((float*)x, (const float*)y, count,
+                                      first ? 1 : 0);
+  CNMF_CUDA(cudaGetLastError());
+  return CNMF_OK;
+}
+
+// A outside device memory (host memory; page-locked memory gives the full
+// copy rate), streamed in row blocks: each block is copied into one device
+// buffer with a 16-byte-aligned row pitch and goes through the device path;
+// the blocks' shares of A^T Y are added in block order, so the result does
+// not depend on timing.  The m x d and n x d panels, their
+// orthonormalisation (CholeskyQR2: its Gram matrices are sums over row
+// blocks of the resident panels, the one central reduction that TSQR plays
+// in the paper's out-of-core setting) and A-tilde stay in device memory.
+struct HostSource : PassSource {
+  const void* A;
+  cnmf_dtype a_type;
+  int64_t m, n, lda;
+  int d;
+  int64_t rows_blk;
+  void* blk;         // rows_blk x ldb, a_type
+  int64_t ldb;
+  void* znb;         // n x KP, the block's share of A^T Y
+  const CompressLayout* lay;
+  int32_t* status;
+  cudaStream_t s;
+
+  size_t es() const {
+    return a_type == CNMF_F64 ? 8 : (a_type == CNMF_F32 ? 4 : 2);
+  }
+  cnmf_status copy(int64_t i0, int64_t mb) {
+    const size_t e = es();
+    CNMF_CUDA(cudaMemcpy2DAsync(blk, (size_t)ldb * e,
+                                (const char*)A + (size_t)i0 * lda * e,
+                                (size_t)lda * e, (size_t)n * e, (size_t)mb,
+                                cudaMemcpyDefault, s));
+    return CNMF_OK;
+  }
+  DeviceSource block(int64_t mb) const {
+    DeviceSource b;
+    b.A = blk; b.a_type = a_type; b.m = mb; b.n = n; b.lda = ldb; b.d = d;
+    b.lay = lay; b.status = status; b.s = s;
+    return b;
+  }
+  cnmf_status both(const void* X, int64_t ldx, const void* Y, int64_t ldy,
+                   void* zm, void* zn) override {
+    const size_t w = wbytes(work_type(a_type));
+    const int KP = lay->KP;
+    for (int64_t i0 = 0; i0 < m; i0 += rows_blk) {
+      const int64_t mb = std::min(rows_blk, m - i0);
+      CNMF_TRY(copy(i0, mb));
+      DeviceSource b = block(mb);
+      CNMF_TRY(b.both(X, ldx, (const char*)Y + (size_t)i0 * ldy * w, ldy,
+                      (char*)zm + (size_t)i0 * KP * w, znb));
+      CNMF_TRY(launch_acc(zn, znb, n * (int64_t)KP, i0 == 0,
+                          work_type(a_type), s));
+    }
+    return CNMF_OK;
+  }
+  cnmf_status left(const void* X, int64_t ldx, void* zm) override {
+    const size_t w = wbytes(work_type(a_type));
+    const int KP = lay->KP;
+    for (int64_t i0 = 0; i0 < m; i0 += rows_blk) {
+      const int64_t mb = std::min(rows_blk, m - i0);
+      CNMF_TRY(copy(i0, mb));
+      DeviceSource b = block(mb);
+      CNMF_TRY(b.left(X, ldx, (char*)zm + (size_t)i0 * KP * w));
+    }
+    return CNMF_OK;
+  }
+};
+
+struct HostLayout {
+  CompressLayout lay;
+  int64_t rows_blk, ldb;
+  void *blk, *znb;
+  size_t bytes;
+};
+
+static HostLayout host_layout(void* ws, int64_t m, int64_t n, int d,
+                              cnmf_dtype a_type, int64_t block_rows) {
+  HostLayout H;
+  H.rows_blk = std::min(block_rows, m);
+  H.lay = compress_layout(ws, m, n, d, a_type, H.rows_blk);
+  const size_t e = a_type == CNMF_F64 ? 8 : (a_type == CNMF_F32 ? 4 : 2);
+  H.ldb = (n + 7) / 8 * 8;
+  Carve cv(ws ? (char*)ws + H.lay.bytes : nullptr, SIZE_MAX);
+  H.blk = cv.take<char>((size_t)H.rows_blk * H.ldb * e);
+  H.znb = cv.take<char>((size_t)n * H.lay.KP * wbytes(work_type(a_type)));
+  H.bytes = H.lay.bytes + cv.off;
+  return H;
+}
+
+// Alg. 1 on A and A^T (2q + 1 passes with re-orthonormalisation), then
+// A-check and A-tilde, over any source of passes.
+static cnmf_status compress_passes(PassSource& src, cnmf_dtype a_type,
+                                   int64_t m, int64_t n, int r, int d, int q,
+                                   uint64_t seed, const void* Omega,
+                                   const void* Psi, void* L, void* Rt,
+                                   void* Atilde, const CompressLayout& lay,
+                                   int32_t* dev_status, cudaStream_t s) {
+  (void)r;
   const cnmf_dtype w = work_type(a_type);
   const int KP = lay.KP;
-
   const void* X = Omega;   // n x d operand of the A-product
   int64_t ldx = d;
   const void* Y = Psi;     // m x d operand of the A^T-product
@@ -186,22 +340,11 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
   void* mb[2] = {lay.m0, lay.m1};
   void* nb[2] = {lay.n0, lay.n1};
   const int T = 2 * q + 1;
-  const bool fused = fused_applicable(A, a_type, m, n, lda, d);
   for (int t = 0; t < T; ++t) {
     const bool last = (t == T - 1);
     void* zm = mb[t & 1];
     void* zn = nb[t & 1];
-    if (fused) {
-      // both products of the pass from one read of A
-      FusedArgs fa{A, a_type, m, n, lda, X, ldx, Y, ldy, d, zm, KP, zn, KP,
-                   dev_status};
-      CNMF_TRY(launch_fused(fa, lay.prod_ws, lay.prod_bytes, s));
-    } else {
-      ProdArgs pa{A, a_type, m, n, lda, false, X, ldx, d, zm, KP, d, dev_status};
-      CNMF_TRY(launch_prod(pa, lay.prod_ws, lay.prod_bytes, s));
-      ProdArgs pt{A, a_type, m, n, lda, true, Y, ldy, d, zn, KP, d, dev_status};
-      CNMF_TRY(launch_prod(pt, lay.prod_ws, lay.prod_bytes, s));
-    }
+    CNMF_TRY(src.both(X, ldx, Y, ldy, zm, zn));
     OrthPanel op[2] = {{zm, m, KP, last ? L : zm, last ? d : KP},
                        {zn, n, KP, last ? Rt : zn, last ? d : KP}};
     // the last pass gives L and R^T: the unique thin Q (CholeskyQR2); in
@@ -215,10 +358,36 @@ extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
     Y = zm; ldy = KP;
   }
   // A-check = A R^T (m x d), then A-tilde = L^T A-check (d x d)
-  CNMF_TRY(acheck_product(A, a_type, m, n, lda, Rt, d, lay, dev_status, s));
+  CNMF_TRY(src.left(Rt, d, lay.acheck));
   CNMF_TRY(launch_cross(L, d, lay.acheck, KP, m, d, w, Atilde, d, lay.orth_ws,
                         lay.orth_bytes, s));
   return CNMF_OK;
+}
+
+}  // namespace cnmf
+
+using namespace cnmf;
+
+extern "C" cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type,
+                                     int64_t m, int64_t n, int64_t lda,
+                                     int32_t r, int32_t d, int32_t q,
+                                     uint64_t seed, const void* Omega,
+                                     const void* Psi, void* L, void* Rt,
+                                     void* Atilde, void* ws, size_t ws_bytes,
+                                     int32_t* dev_status,
+                                     cnmf_stream_t stream) {
+  if (!valid_type(a_type) || !A || !L || !Rt || !Atilde || !ws || m < 1 ||
+      n < 1 || lda < n || r < 1 || d < r || d > 128 || d > m || d > n ||
+      q < 0 || q > 64)
+    return CNMF_E_INVALID_ARG;
+  CompressLayout lay = compress_layout(ws, m, n, d, a_type);
+  if (ws_bytes < lay.bytes) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceSource src;
+  src.A = A; src.a_type = a_type; src.m = m; src.n = n; src.lda = lda;
+  src.d = d; src.lay = &lay; src.status = dev_status; src.s = s;
+  return compress_passes(src, a_type, m, n, r, d, q, seed, Omega, Psi, L, Rt,
+                         Atilde, lay, dev_status, s);
 }
 
 extern "C" cnmf_status cnmf_compress_gaussian(const void* A, cnmf_dtype a_type,
@@ -250,4 +419,37 @@ extern "C" cnmf_status cnmf_compress_gaussian(const void* A, cnmf_dtype a_type,
   CNMF_TRY(launch_cross(L, d, lay.acheck, KP, m, d, w, Atilde, d, lay.orth_ws,
                         lay.orth_bytes, s));
   return CNMF_OK;
+}
+
+extern "C" size_t cnmf_compress_host_workspace(int64_t m, int64_t n, int32_t d,
+                                               cnmf_dtype a_type,
+                                               int64_t block_rows) {
+  if (m < 1 || n < 1 || d < 1 || d > 128 || block_rows < 1 ||
+      !valid_type(a_type))
+    return 0;
+  return host_layout(nullptr, m, n, d, a_type, block_rows).bytes;
+}
+
+extern "C" cnmf_status cnmf_compress_host(const void* A, cnmf_dtype a_type,
+                                          int64_t m, int64_t n, int64_t lda,
+                                          int32_t r, int32_t d, int32_t q,
+                                          uint64_t seed, const void* Omega,
+                                          const void* Psi, void* L, void* Rt,
+                                          void* Atilde, int64_t block_rows,
+                                          void* ws, size_t ws_bytes,
+                                          int32_t* dev_status,
+                                          cnmf_stream_t stream) {
+  if (!valid_type(a_type) || !A || !L || !Rt || !Atilde || !ws || m < 1 ||
+      n < 1 || lda < n || r < 1 || d < r || d > 128 || d > m || d > n ||
+      q < 0 || q > 64 || block_rows < 1)
+    return CNMF_E_INVALID_ARG;
+  HostLayout H = host_layout(ws, m, n, d, a_type, block_rows);
+  if (ws_bytes < H.bytes) return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  HostSource src;
+  src.A = A; src.a_type = a_type; src.m = m; src.n = n; src.lda = lda;
+  src.d = d; src.rows_blk = H.rows_blk; src.blk = H.blk; src.ldb = H.ldb;
+  src.znb = H.znb; src.lay = &H.lay; src.status = dev_status; src.s = s;
+  return compress_passes(src, a_type, m, n, r, d, q, seed, Omega, Psi, L, Rt,
+                         Atilde, H.lay, dev_status, s);
 }

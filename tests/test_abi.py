@@ -152,6 +152,23 @@ def test_als_and_gaussian_compression_invalid_arguments(lib):
     assert mu(iters=-1) == E
     assert mu(r=65, d=70) == E
     assert lib.cnmf_factor_mu_workspace(100, 80, 11, 10, 1) == 0
+    # cnmf_compress_host(A, a_type, m, n, lda, r, d, q, seed, Omega, Psi, L,
+    #                    Rt, Atilde, block_rows, ws, ws_bytes, status, stream)
+    def ch(**kw):
+        a = dict(m=100, n=80, lda=80, r=4, d=10, q=2, blk=16)
+        a.update(kw)
+        return lib.cnmf_compress_host(f, 1, a["m"], a["n"], a["lda"], a["r"],
+                                      a["d"], a["q"], 1, None, None, f, f, f,
+                                      a["blk"], f, 1 << 30, None, None)
+    assert ch(blk=0) == E
+    assert ch(lda=79) == E
+    assert ch(d=81) == E
+    assert ch(r=11) == E
+    assert ch(q=-1) == E
+    assert lib.cnmf_compress_host_workspace(100, 80, 10, 1, 0) == 0
+    assert lib.cnmf_compress_host_workspace(100, 80, 10, 1, 16) > 0
+    assert lib.cnmf_compress_host(f, 1, 100, 80, 80, 4, 10, 2, 1, None, None,
+                                  f, f, f, 16, f, 16, None, None) == 2
     assert lib.cnmf_factor_mu_workspace(100, 80, 4, 10, 1) == \
         lib.cnmf_factor_als_workspace(100, 80, 4, 10, 1)
     # cnmf_compress_gaussian(A, a_type, m, n, lda, d, seed, L, Rt, Atilde,
