@@ -36,7 +36,10 @@
  *     matrix that is not numerically positive definite), CNMF_E_NONFINITE
  *     (NaN/Inf met in a panel or factor), CNMF_E_TIMEOUT (a bounded grid
  *     barrier wait expired; the kernel returns instead of hanging).
- *     The caller reads *dev_status after synchronising the stream.
+ *     The caller reads *dev_status after synchronising the stream.  The
+ *     error code is (*dev_status & CNMF_STATUS_CODE_MASK); the high bits
+ *     are flags that are not errors (CNMF_STATUS_NEGATIVE_A, set by
+ *     cnmf_check_nonnegative), kept beside the error code.
  *   - Working precision W: FP64 when the input type is CNMF_F64, else FP32.
  *     Outputs and test matrices are in W.  A stored as CNMF_BF16 is widened
  *     to FP32 on load.
@@ -64,6 +67,11 @@ typedef enum {
   CNMF_E_NONFINITE = 5,
   CNMF_E_TIMEOUT = 6
 } cnmf_status;
+
+/* Bits of *dev_status: the error code (a cnmf_status) in the low bits, and
+ * flags that are not errors in the high bits. */
+#define CNMF_STATUS_CODE_MASK 0x0000FFFF
+#define CNMF_STATUS_NEGATIVE_A 0x40000000 /* A holds an entry below zero */
 
 /* Storage type of A (and, for CNMF_F64 / CNMF_F32, of W-typed buffers). */
 typedef enum { CNMF_F64 = 0, CNMF_F32 = 1, CNMF_BF16 = 2 } cnmf_dtype;
@@ -175,7 +183,8 @@ cnmf_status cnmf_orth(void* Y, cnmf_dtype w_type, int64_t rows, int32_t k,
  * A^T, Sec. III) with q power iterations and re-orthonormalisation after
  * every product, then A-tilde = L^T A R^T (Alg. 4 setup).
  *   A       m x n, a_type, pitch lda (>= n).  NMF expects A >= 0 (Sec. I);
- *           negative entries are not rejected.
+ *           negative entries are not rejected (cnmf_check_nonnegative
+ *           reports them).
  *   r, d    target rank and sketch size d = r + r_ov, 1 <= r <= d <=
  *           min(m, n), d <= 128.
  *   q       power iterations (Alg. 1 exponent w), 0 <= q <= 64.  The
@@ -464,6 +473,21 @@ cnmf_status cnmf_residual(const void* A, cnmf_dtype a_type, int64_t m,
                           const void* Vt, cnmf_dtype w_type, int32_t r,
                           double* out2, void* ws, size_t ws_bytes,
                           cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cnmf_check_nonnegative: reports whether A holds a negative entry.  NMF and
+ * SNMF are posed for a nonnegative matrix (Sec. II, the NMF problem; Sec.
+ * IV, separable NMF); the compression itself is defined for any A, so a
+ * negative entry is reported, not rejected: the flag bit
+ * CNMF_STATUS_NEGATIVE_A is ORed into *dev_status (required, device
+ * int32), keeping the error code in its low bits.  An entry is negative
+ * when it compares below zero (-0.0 and NaN are not).  Only the n entries
+ * of each row are read, not the padding up to lda.  One read of A; the
+ * compression entry points do not run it by themselves.
+ * ---------------------------------------------------------------------- */
+cnmf_status cnmf_check_nonnegative(const void* A, cnmf_dtype a_type,
+                                   int64_t m, int64_t n, int64_t lda,
+                                   int32_t* dev_status, cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * cnmf_residual_noalloc: the same result as cnmf_residual, for callers that

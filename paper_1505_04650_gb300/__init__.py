@@ -89,10 +89,28 @@ def _status(dev):
 
 
 def raise_on_status(status: torch.Tensor, where: str):
-    """Synchronising check of a device status word (first error wins)."""
-    code = int(status.item())
+    """Synchronising check of a device status word (first error wins; the
+    flag bits, which are not errors, are ignored)."""
+    code = int(status.item()) & _lib.CNMF_STATUS_CODE_MASK
     if code != _lib.CNMF_OK:
         raise CnmfError(code, where)
+
+
+def has_negative_entries(status: torch.Tensor) -> bool:
+    """Synchronising read of the flag that cnmf_check_nonnegative sets."""
+    return bool(int(status.item()) & _lib.CNMF_STATUS_NEGATIVE_A)
+
+
+def cnmf_check_nonnegative(A: torch.Tensor,
+                           status: torch.Tensor | None = None):
+    """ORs the negative-entry flag into the status word if A holds an entry
+    below zero (NMF assumes A >= 0, Sec. II); returns the status word."""
+    m, n, lda = _mat(A)
+    st = status if status is not None else _status(A.device)
+    _check(lib().cnmf_check_nonnegative(_ptr(A), _DT[A.dtype], m, n, lda,
+                                        _ptr(st), _stream(A.device)),
+           "cnmf_check_nonnegative")
+    return st
 
 
 def sketch_size(r: int, r_ov: int, n: int) -> int:

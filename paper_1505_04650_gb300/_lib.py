@@ -17,6 +17,9 @@ c_void_p, c_size_t, c_int32, c_int64, c_uint32, c_uint64, c_double = (
 # status codes and storage types (cnmf.h)
 CNMF_OK, CNMF_E_INVALID_ARG, CNMF_E_WORKSPACE, CNMF_E_CUDA = 0, 1, 2, 3
 CNMF_E_CHOLESKY, CNMF_E_NONFINITE, CNMF_E_TIMEOUT = 4, 5, 6
+# bits of the device status word: error code low, flags (not errors) high
+CNMF_STATUS_CODE_MASK = 0x0000FFFF
+CNMF_STATUS_NEGATIVE_A = 0x40000000
 CNMF_F64, CNMF_F32, CNMF_BF16 = 0, 1, 2
 
 
@@ -118,6 +121,9 @@ SIGNATURES = {
     "cnmf_residual": (c_int32, [c_void_p, c_int32, c_int64, c_int64, c_int64,
                                 c_void_p, c_void_p, c_int32, c_int32,
                                 c_void_p, c_void_p, c_size_t, c_void_p]),
+    "cnmf_check_nonnegative": (c_int32, [c_void_p, c_int32, c_int64,
+                                         c_int64, c_int64, c_void_p,
+                                         c_void_p]),
     "cnmf_residual_noalloc": (c_int32, [c_void_p, c_int32, c_int64, c_int64,
                                         c_int64, c_void_p, c_void_p, c_int32,
                                         c_int32, c_void_p, c_void_p]),

@@ -1,4 +1,5 @@
 // Status strings, ABI version and device queries.
+#include <cstdlib>
 #include <cstdio>
 #include <mutex>
 
@@ -30,6 +31,11 @@ int num_sms() {
   }
   const int full = cached[dev];
   return (t_cta_limit > 0 && t_cta_limit < full) ? t_cta_limit : full;
+}
+
+bool pdl_enabled() {
+  static const bool on = getenv("CNMF_NO_PDL") == nullptr;
+  return on;
 }
 
 int max_smem_optin() {

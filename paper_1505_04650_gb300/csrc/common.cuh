@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "cnmf.h"
 
 namespace cnmf {
@@ -99,10 +101,17 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ---------------------------------------------------------------------------
-// Status word: the first device-detected error wins.
+// Status word: the first device-detected error wins; flag bits
+// (CNMF_STATUS_NEGATIVE_A) are kept beside it and do not count as an error.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(int32_t* st, int32_t code) {
-  if (st) atomicCAS(st, 0, code);
+  if (!st) return;
+  int32_t old = atomicCAS(st, 0, code);   // the common case: no flag set
+  while (old != 0 && (old & CNMF_STATUS_CODE_MASK) == 0) {
+    const int32_t prev = atomicCAS(st, old, old | code);
+    if (prev == old) return;
+    old = prev;
+  }
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -251,6 +260,46 @@ struct Carve {
   }
   __host__ bool fits() const { return off <= cap; }
 };
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of a pass chain (sketch pass,
+// CholeskyQR) are launched with programmatic stream serialisation, so a
+// kernel's CTAs can be scheduled, and run their set-up, while the kernel
+// before it in the stream finishes.  Every kernel so launched calls
+// pdl_wait() before it touches memory that an earlier kernel writes or
+// reads (griddepcontrol.wait returns once the preceding grid has completed
+// and its writes are visible; it returns at once in a normally launched
+// kernel).  Because each kernel of the chain waits before it completes,
+// the wait covers every earlier kernel of the stream, not only the one
+// before.  A kernel calls pdl_release() to let the next kernel launch
+// before it ends (without it, the next one launches as its CTAs exit).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+bool pdl_enabled();   // false with CNMF_NO_PDL set in the environment
+
+// kernel<<<grid, block, smem, s>>>(args...) with programmatic stream
+// serialisation (where enabled); the launch error is left for
+// CNMF_CHECK_LAUNCH.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block,
+                       size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 int num_sms();                       // SM count of the current device
 int max_smem_optin();                // opt-in shared memory per block (bytes)

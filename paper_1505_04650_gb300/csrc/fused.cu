@@ -162,6 +162,10 @@ __global__ void k_fu_pack(const float* __restrict__ X, int64_t ldx, int64_t n,
                           int kb, int KP, bf16* __restrict__ Xp, int64_t spn,
                           bf16* __restrict__ Yp, int64_t spm) {
   __shared__ float tile[32][33];
+  // X, Y come from the kernel before; once they can be read, the fused
+  // pass may launch and start its loads of A
+  pdl_wait();
+  pdl_release();
   const bool xs = blockIdx.z == 0;
   const float* B = xs ? X : Y;
   if (!B) return;
@@ -226,7 +230,8 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[4], conv_bar[4], empty_bar[4];
   __shared__ __align__(8) uint64_t y_full[2], y_empty[2];
-  __shared__ __align__(8) uint64_t z1_full[2], z1_empty[2], z2_full, z2_empty,
+  __shared__ __align__(8) uint64_t z1_full[2], z1_empty[2], z2_full,
+      z2_empty[16],
       drain_bar[2];
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
       mbar_init(&drain_bar[i], 1);
     }
     mbar_init(&z2_full, 1);
-    mbar_init(&z2_empty, 128);
+    for (int i = 0; i < 16; ++i) mbar_init(&z2_empty[i], 128);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -281,9 +286,31 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
     int s = 0;
     uint32_t ph = 0;
     int64_t nissued = 0;
-    FuPos p;
+    FuPos p, pd;
     fu_decode(geo, u0, p);
+    pd = p;
+    // The first min(ST, tiles) stages get their A tiles before the wait for
+    // the kernel before (A is no output of it); their X tiles, which it
+    // writes, follow the wait, before any stage is reused.
+    const int64_t npre = u1 - u0 < ST ? u1 - u0 : ST;
+    bool waited = false;
+    auto load_x = [&](int st, const FuPos& q) {
+      unsigned char* sx = smem + (size_t)st * C::STAGE + C::A_BYTES;
+      const int jt = q.g * geo.Tj + q.jl;
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        tma_load_2d(sx + b * C::P_BOX, &tmX, jt * FU_T + b * 64, 0,
+                    &full_bar[st]);
+    };
+    auto release_x = [&]() {
+      pdl_wait();
+      waited = true;
+      if (!hx) return;
+      for (int64_t t = 0; t < nissued && t < npre; ++t, fu_next(geo, pd))
+        load_x((int)t, pd);
+    };
     for (int64_t u = u0; u < u1; ++u, fu_next(geo, p)) {
+      if (!waited && u - u0 == npre) release_x();
       if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_s, status)) break;
       unsigned char* sa = smem + (size_t)s * C::STAGE;
       const int jt = p.g * geo.Tj + p.jl;
@@ -292,15 +319,11 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
       for (int b = 0; b < C::NBOX; ++b)
         tma_load_2d_hint(sa + b * FU_BOX, &tmA, jt * FU_T + b * C::BOXW,
                          p.i * FU_T, &full_bar[s], pol);
-      if (hx) {
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-          tma_load_2d(sa + C::A_BYTES + b * C::P_BOX, &tmX,
-                      jt * FU_T + b * 64, 0, &full_bar[s]);
-      }
+      if (hx && waited) load_x(s, p);
       ++nissued;
       if (++s == ST) { s = 0; ph ^= 1u; }
     }
+    if (!waited) release_x();
     // every copy has landed before exit (bounded): the last ST loads
     for (int64_t t = nissued - 1; t >= 0 && t >= nissued - ST; --t) {
       uint64_t* fb = &full_bar[t % ST];
@@ -311,6 +334,7 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
     }
   } else if (warp == 2 && lane == 0) {
     // ---------------- TMA: Y tile per row segment ----------------
+    pdl_wait();   // Y comes from the kernel before
     if (hy) {
       int yb = 0;
       uint32_t yph = 0;
@@ -349,7 +373,10 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
     const bool is_x = warp == 1;
     if ((is_x && hx) || (!is_x && hy)) {
       int s = 0, zb = 0, yb = 0;
-      uint32_t ph = 0, zph = 0, yph = 0, z2ph = 0;
+      uint32_t ph = 0, zph = 0, yph = 0;
+      // bit jl: parity of the number of drains of A^T Y accumulator jl so
+      // far (the epilogue drains columns 0 .. w - 1 at every run's end)
+      uint32_t drained = 0;
       uint32_t touched = 0;
       bool any = false;
       const uint32_t smem0 = smem_u32(smem);
@@ -367,10 +394,14 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
               !mbar_wait(&z1_empty[zb], zph ^ 1u, &abort_s, status))
             break;
         } else {
-          if (run_first) {
-            if (!mbar_wait(&z2_empty, z2ph ^ 1u, &abort_s, status)) break;
-            touched = 0;
-          }
+          if (run_first) touched = 0;
+          // the first MMA of a run into accumulator jl waits only for the
+          // epilogue to have drained that accumulator, so a new run starts
+          // while the previous run's other columns are still being drained
+          if (((touched >> p.jl) & 1u) == 0 &&
+              !mbar_wait(&z2_empty[p.jl], ((drained >> p.jl) & 1u) ^ 1u,
+                         &abort_s, status))
+            break;
           if (seg_first && !mbar_wait(&y_full[yb], yph, &abort_s, status))
             break;
         }
@@ -426,7 +457,7 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
           if (seg_last) tc_commit(&y_empty[yb]);
           if (run_last) tc_commit(&z2_full);
           if (seg_last && ++yb == YB) { yb = 0; yph ^= 1u; }
-          if (run_last) z2ph ^= 1u;
+          if (run_last) drained ^= p.w >= 32 ? ~0u : (1u << p.w) - 1u;
         }
         any = true;
         if (++s == ST) { s = 0; ph ^= 1u; }
@@ -485,6 +516,7 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
     // reads has been written.  A slot is stored column by column (element
     // (r, j) at j 128 + r), so a warp's store of one column is one 128-byte
     // line.
+    pdl_wait();   // the partial slots were read by the kernels before
     const int q = warp - 4;                 // tensor-memory lane quarter
     const int row = 32 * q + lane;          // row of the accumulators
     const uint32_t tl = (uint32_t)(32 * q) << 16;
@@ -543,9 +575,9 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
 #pragma unroll
             for (int t = 0; t < 16; ++t) dst[(size_t)(c0 + t) * FU_T] = v[t];
           }
+          tc_fence_before();
+          mbar_arrive(&z2_empty[jl]);
         }
-        tc_fence_before();
-        mbar_arrive(&z2_empty);
       }
     }
   }
@@ -562,14 +594,15 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
 }
 
 // ---------------------------------------------------------------------------
-// Sum of the partial slots, in a fixed order.  With A X formed, blocks
-// 0 .. TI - 1 make the 128-row tiles of Zm = A X: for each group in order,
+// Sum of the partial slots, in a fixed order.  With A X formed, tiles
+// 0 .. TI - 1 are the 128-row tiles of Zm = A X: for each group in order,
 // the pieces of the row's segment in CTA order.  With A^T Y formed, the
-// next TJ blocks make the 128-row tiles of Zn = A^T Y: the runs of the
-// column's group in CTA order.  Warp 0 lists the slots in shared memory
-// first (one group per lane, then a prefix sum); the threads then add the
-// slots four at a time, each thread owning whole float4s of the tile, so
-// many loads are in flight.
+// next TJ tiles are the 128-row tiles of Zn = A^T Y: the runs of the
+// column's group in CTA order.  Each output tile is split over KP / 8
+// blocks of 256 threads, one float4 of the tile per thread; warp 0 lists
+// the slots in shared memory first (one group per lane, then a prefix
+// sum); each thread then adds its float4 of every slot, eight loads in
+// flight, in slot order.
 // ---------------------------------------------------------------------------
 constexpr int FU_RED_MAX = 2048;
 constexpr int FU_RED_NT = 256;
@@ -577,11 +610,15 @@ constexpr int FU_RED_NT = 256;
 template <int KP>
 __global__ void __launch_bounds__(FU_RED_NT)
     k_fu_reduce(const FuGeom geo, const FuOut out) {
+  constexpr int RQ = FU_T * KP / 4 / FU_RED_NT;   // blocks per tile: 4 / 2
+  static_assert(RQ * FU_RED_NT * 4 == FU_T * KP, "one float4 per thread");
   __shared__ int64_t off[FU_RED_MAX];
   __shared__ int ns_s;
+  pdl_wait();   // the fused pass's partial slots
+  const int tile = (int)blockIdx.x / RQ, part = (int)blockIdx.x % RQ;
   const int nrow_blocks = geo.has_x ? geo.TI : 0;
-  const bool rows = (int)blockIdx.x < nrow_blocks;
-  const int t = rows ? (int)blockIdx.x : (int)blockIdx.x - nrow_blocks;
+  const bool rows = tile < nrow_blocks;
+  const int t = rows ? tile : tile - nrow_blocks;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int ns = 0;
@@ -635,49 +672,33 @@ __global__ void __launch_bounds__(FU_RED_NT)
   float* Z = rows ? out.Zm : out.Zn;
   const int64_t ldz = rows ? out.ldzm : out.ldzn;
   const int64_t P_rows = rows ? out.m : out.n;
-  constexpr int F4 = FU_T * KP / 4;              // float4 per slot
-  constexpr int PER = F4 / FU_RED_NT;            // per thread: 2 or 4
-  static_assert(F4 % FU_RED_NT == 0, "whole float4 per thread");
-  float4 acc[PER];
-#pragma unroll
-  for (int e = 0; e < PER; ++e) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int f = part * FU_RED_NT + (int)threadIdx.x;   // float4 of the tile
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  constexpr int B = 8;
   int k = 0;
-  for (; k + 4 <= ns; k += 4) {
-    float4 v[4][PER];
+  for (; k + B <= ns; k += B) {
+    float4 v[B];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < B; ++a)
+      v[a] = __ldcg(reinterpret_cast<const float4*>(P + off[k + a]) + f);
 #pragma unroll
-      for (int e = 0; e < PER; ++e)
-        v[a][e] = __ldcg(reinterpret_cast<const float4*>(P + off[k + a]) +
-                         threadIdx.x + e * FU_RED_NT);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int e = 0; e < PER; ++e) {
-        acc[e].x += v[a][e].x; acc[e].y += v[a][e].y;
-        acc[e].z += v[a][e].z; acc[e].w += v[a][e].w;
-      }
+    for (int a = 0; a < B; ++a) {
+      acc.x += v[a].x; acc.y += v[a].y; acc.z += v[a].z; acc.w += v[a].w;
+    }
   }
-  for (; k < ns; ++k)
+  for (; k < ns; ++k) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(P + off[k]) + f);
+    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+  }
+  // slots are column-major: float4 f holds rows 4f % 128 .. + 3 of column
+  // 4f / 128
+  const int col = (4 * f) / FU_T, r0 = (4 * f) % FU_T;
+  if (col >= out.kz) return;
+  const float vv[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const float4 v = __ldcg(reinterpret_cast<const float4*>(P + off[k]) +
-                              threadIdx.x + e * FU_RED_NT);
-      acc[e].x += v.x; acc[e].y += v.y; acc[e].z += v.z; acc[e].w += v.w;
-    }
-#pragma unroll
-  for (int e = 0; e < PER; ++e) {
-    // slots are column-major: float4 f holds rows 4f % 128 .. + 3 of
-    // column 4f / 128
-    const int f = threadIdx.x + e * FU_RED_NT;     // float4 index in the tile
-    const int col = (4 * f) / FU_T, r0 = (4 * f) % FU_T;
-    if (col >= out.kz) continue;
-    const float vv[4] = {acc[e].x, acc[e].y, acc[e].z, acc[e].w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t prow = (int64_t)t * FU_T + r0 + q;
-      if (prow < P_rows) Z[prow * ldz + col] = vv[q];
-    }
+  for (int q = 0; q < 4; ++q) {
+    const int64_t prow = (int64_t)t * FU_T + r0 + q;
+    if (prow < P_rows) Z[prow * ldz + col] = vv[q];
   }
 }
 
@@ -785,10 +806,10 @@ static cnmf_status run_fused(const FusedArgs& a, const FuPlan& pl, void* ws,
   // pack the panels
   dim3 pg((unsigned)ceil_div(std::max(pl.spn, pl.spm), 32),
           (unsigned)ceil_div(KP, 32), 2);
-  k_fu_pack<<<pg, 256, 0, s>>>(
-      q.has_x ? (const float*)a.X : nullptr, a.ldx, a.n,
-      q.has_y ? (const float*)a.Y : nullptr, a.ldy, a.m, a.k, KP, Xp, pl.spn,
-      Yp, pl.spm);
+  launch_pdl(k_fu_pack, pg, dim3(256), 0, s,
+             q.has_x ? (const float*)a.X : nullptr, a.ldx, a.n,
+             q.has_y ? (const float*)a.Y : nullptr, a.ldy, a.m, a.k, KP, Xp,
+             pl.spn, Yp, pl.spm);
   CNMF_CHECK_LAUNCH();
   CUtensorMap ta, tx, ty;
   bool ok = make_map(&ta, a.A, F32, (uint64_t)a.n, (uint64_t)a.m,
@@ -800,10 +821,12 @@ static cnmf_status run_fused(const FusedArgs& a, const FuPlan& pl, void* ws,
   if (!ok) return CNMF_E_INVALID_ARG;
   FuOut o{(float*)a.Zm, a.ldzm, (float*)a.Zn, a.ldzn, a.k, a.m, a.n,
           P1, P2, a.status};
-  k_fused_pass<KP, F32><<<(unsigned)q.G, C::NT, C::SMEM, s>>>(ta, tx, ty, q, o);
+  launch_pdl(k_fused_pass<KP, F32>, dim3((unsigned)q.G), dim3(C::NT), C::SMEM,
+             s, ta, tx, ty, q, o);
   CNMF_CHECK_LAUNCH();
-  const int nred = (q.has_x ? q.TI : 0) + (q.has_y ? q.TJ : 0);
-  k_fu_reduce<KP><<<(unsigned)nred, FU_RED_NT, 0, s>>>(q, o);
+  const int nred = ((q.has_x ? q.TI : 0) + (q.has_y ? q.TJ : 0)) * (KP / 8);
+  launch_pdl(k_fu_reduce<KP>, dim3((unsigned)nred), dim3(FU_RED_NT), 0, s, q,
+             o);
   CNMF_CHECK_LAUNCH();
   return CNMF_OK;
 }

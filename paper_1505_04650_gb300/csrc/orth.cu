@@ -175,9 +175,15 @@ struct RowTile {
 // Gram (SYM) or cross products over row ranges; per-CTA partials, FP64.
 template <typename W, int KP, bool SYM>
 __global__ void __launch_bounds__(OR_NT)
-    k_gram(PanelDesc p0, PanelDesc p1, int k, double* __restrict__ part) {
+    k_gram(PanelDesc p0, PanelDesc p1, int k, double* __restrict__ part,
+           unsigned* __restrict__ tickets) {
   typedef GramMap<KP, SYM> M;
   extern __shared__ __align__(16) unsigned char smem[];
+  pdl_wait();   // the panels come from the kernels before
+  // the tickets of the k_finish launches that follow start at zero (each
+  // k_finish's last CTA puts its ticket back to zero)
+  if (tickets && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 2)
+    tickets[threadIdx.x] = 0u;
   W* Xs = reinterpret_cast<W*>(smem);
   W* Ys = SYM ? Xs : Xs + OR_ROWS * M::PITCH;
   const PanelDesc& P = blockIdx.y ? p1 : p0;
@@ -309,6 +315,7 @@ __global__ void __launch_bounds__(OR_NT)
   // (thread j takes partials j, j + FIN_S, ...), then one thread adds the
   // FIN_S sub-sums in order -- a fixed order, so the result is deterministic.
   constexpr int FIN_S = OR_NT / FIN_E;
+  pdl_wait();   // the Gram partials
   __shared__ double red[FIN_E][FIN_S + 1];
   const int p = blockIdx.y;
   const int le = threadIdx.x / FIN_S, sub = threadIdx.x % FIN_S;
@@ -509,6 +516,7 @@ __global__ void __launch_bounds__(OR_NT)
   constexpr int PITCH = KP + 4;
   constexpr int TN = KP / 8;
   extern __shared__ __align__(16) unsigned char smem[];
+  pdl_wait();   // R^-1 from k_finish, the panel
   W* Rs = reinterpret_cast<W*>(smem);        // KP x KP
   W* Ys = Rs + KP * KP;                      // OR_ROWS x PITCH
   W* Qs = Ys + OR_ROWS * PITCH;              // OR_ROWS x PITCH
@@ -618,8 +626,7 @@ static cnmf_status run_orth(const OrthPanel* pp, int np, int k, void* ws,
   double* part = cv.take<double>((size_t)2 * G * KP * KP);
   double* gfull = cv.take<double>((size_t)2 * KP * KP);
   W* rinv = cv.take<W>((size_t)2 * KP * KP);
-  unsigned* tickets = cv.take<unsigned>(64);
-  CNMF_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s));
+  unsigned* tickets = cv.take<unsigned>(64);   // zeroed by k_gram
   PanelDesc d[2];
   for (int i = 0; i < 2; ++i) {
     const OrthPanel& o = pp[std::min(i, np - 1)];
@@ -631,30 +638,33 @@ static cnmf_status run_orth(const OrthPanel* pp, int np, int k, void* ws,
   const size_t ap_smem = apply_smem<W, KP>();
   const double shift = sizeof(W) == 8 ? 1e-13 : 1e-11;
 
-  k_gram<W, KP, true><<<grid, OR_NT, gram_smem<W, KP, true>(), s>>>(
-      d[0], d[1], k, part);
+  launch_pdl(k_gram<W, KP, true>, grid, dim3(OR_NT), gram_smem<W, KP, true>(),
+             s, d[0], d[1], k, part, tickets);
   CNMF_CHECK_LAUNCH();
-  k_finish<W, KP><<<dim3(nfin, np), OR_NT, fin_smem, s>>>(
-      part, G, k, 1, shift, 0.0, gfull, rinv, rinv + KP * KP, 0, tickets, status);
+  launch_pdl(k_finish<W, KP>, dim3(nfin, np), dim3(OR_NT), fin_smem, s, part,
+             (int64_t)G, k, 1, shift, 0.0, gfull, rinv, rinv + KP * KP,
+             (int64_t)0, tickets, status);
   CNMF_CHECK_LAUNCH();
   W* q0 = (W*)pp[0].Q;
   W* q1 = (W*)pp[std::min(1, np - 1)].Q;
   if (sweeps == 1) {
-    k_apply<W, KP, false><<<grid, OR_NT, ap_smem, s>>>(
-        d[0], d[1], q0, q1, pp[0].ldo, pp[std::min(1, np - 1)].ldo, k, rinv,
-        part);
+    launch_pdl(k_apply<W, KP, false>, grid, dim3(OR_NT), ap_smem, s, d[0],
+               d[1], q0, q1, pp[0].ldo, pp[std::min(1, np - 1)].ldo, k,
+               (const W*)rinv, part);
     CNMF_CHECK_LAUNCH();
     return CNMF_OK;
   }
-  k_apply<W, KP, true><<<grid, OR_NT, ap_smem, s>>>(
-      d[0], d[1], (W*)d[0].Y, (W*)d[1].Y, d[0].ldy, d[1].ldy, k, rinv, part);
+  launch_pdl(k_apply<W, KP, true>, grid, dim3(OR_NT), ap_smem, s, d[0], d[1],
+             (W*)d[0].Y, (W*)d[1].Y, d[0].ldy, d[1].ldy, k, (const W*)rinv,
+             part);
   CNMF_CHECK_LAUNCH();
-  k_finish<W, KP><<<dim3(nfin, np), OR_NT, fin_smem, s>>>(
-      part, G, k, 1, 0.0, 0.0, gfull, rinv, rinv + KP * KP, 0, tickets, status);
+  launch_pdl(k_finish<W, KP>, dim3(nfin, np), dim3(OR_NT), fin_smem, s, part,
+             (int64_t)G, k, 1, 0.0, 0.0, gfull, rinv, rinv + KP * KP,
+             (int64_t)0, tickets, status);
   CNMF_CHECK_LAUNCH();
-  k_apply<W, KP, false><<<grid, OR_NT, ap_smem, s>>>(
-      d[0], d[1], q0, q1, pp[0].ldo, pp[std::min(1, np - 1)].ldo, k, rinv,
-      part);
+  launch_pdl(k_apply<W, KP, false>, grid, dim3(OR_NT), ap_smem, s, d[0], d[1],
+             q0, q1, pp[0].ldo, pp[std::min(1, np - 1)].ldo, k, (const W*)rinv,
+             part);
   CNMF_CHECK_LAUNCH();
   return CNMF_OK;
 }
@@ -668,13 +678,14 @@ static cnmf_status run_cross(const void* X, int64_t ldx, const void* Y,
   Carve cv(ws, SIZE_MAX);
   double* part = cv.take<double>((size_t)2 * G * KP * KP);
   PanelDesc d{X, Y, ldx, ldy, rows};
-  k_gram<W, KP, false><<<dim3(G, 1), OR_NT,
-                         gram_smem<W, KP, false>(), s>>>(d, d, k,
-                                                                  part);
+  launch_pdl(k_gram<W, KP, false>, dim3(G, 1), dim3(OR_NT),
+             gram_smem<W, KP, false>(), s, d, d, k, part,
+             (unsigned*)nullptr);
   CNMF_CHECK_LAUNCH();
   const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
-  k_finish<W, KP><<<dim3(nfin, 1), OR_NT, 0, s>>>(
-      part, G, k, 0, 0.0, 0.0, nullptr, (W*)C, (W*)C, ldc, nullptr, nullptr);
+  launch_pdl(k_finish<W, KP>, dim3(nfin, 1), dim3(OR_NT), 0, s, part,
+             (int64_t)G, k, 0, 0.0, 0.0, (double*)nullptr, (W*)C, (W*)C, ldc,
+             (unsigned*)nullptr, (int32_t*)nullptr);
   CNMF_CHECK_LAUNCH();
   return CNMF_OK;
 }
@@ -689,17 +700,16 @@ static cnmf_status run_gram_chol(const void* Y, int64_t ld, int64_t rows,
   double* part = cv.take<double>((size_t)2 * G * KP * KP);
   double* gfull = cv.take<double>((size_t)2 * KP * KP);
   cv.take<W>((size_t)2 * KP * KP);
-  unsigned* tickets = cv.take<unsigned>(64);
-  CNMF_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s));
+  unsigned* tickets = cv.take<unsigned>(64);   // zeroed by k_gram
   PanelDesc d{Y, Y, ld, ld, rows};
-  k_gram<W, KP, true><<<dim3(G, 1), OR_NT, gram_smem<W, KP, true>(), s>>>(
-      d, d, k, part);
+  launch_pdl(k_gram<W, KP, true>, dim3(G, 1), dim3(OR_NT),
+             gram_smem<W, KP, true>(), s, d, d, k, part, tickets);
   CNMF_CHECK_LAUNCH();
   const int nfin = (int)ceil_div((int64_t)KP * KP, FIN_E);
   const size_t fin_smem = finish_smem<W, KP>();
-  k_finish<W, KP><<<dim3(nfin, 1), OR_NT, fin_smem, s>>>(
-      part, G, k, 1, 0.0, shift_abs, gfull, (W*)rinv_out, (W*)rinv_out, 0,
-      tickets, status);
+  launch_pdl(k_finish<W, KP>, dim3(nfin, 1), dim3(OR_NT), fin_smem, s, part,
+             (int64_t)G, k, 1, 0.0, shift_abs, gfull, (W*)rinv_out,
+             (W*)rinv_out, (int64_t)0, tickets, status);
   CNMF_CHECK_LAUNCH();
   return CNMF_OK;
 }

@@ -181,3 +181,30 @@ def test_als_and_gaussian_compression_invalid_arguments(lib):
                                       1 << 30, None, None) == E
     assert lib.cnmf_compress_gaussian(f, 1, 100, 80, 80, 8, 1, f, f, f, f,
                                       16, None, None) == 2   # CNMF_E_WORKSPACE
+
+
+def test_check_nonnegative_invalid_arguments(lib):
+    """The negative-entry check rejects NULL pointers, unknown types, empty
+    shapes and a pitch below n on the host (no GPU work)."""
+    c = C.c_void_p
+    a, st = c(0x1000), c(0x2000)
+    f = lib.cnmf_check_nonnegative
+    assert f(c(0), 1, 10, 10, 10, st, None) == 1
+    assert f(a, 1, 10, 10, 10, c(0), None) == 1
+    assert f(a, 9, 10, 10, 10, st, None) == 1
+    assert f(a, 1, 0, 10, 10, st, None) == 1
+    assert f(a, 1, 10, 0, 10, st, None) == 1
+    assert f(a, 1, 10, 10, 9, st, None) == 1
+
+
+def test_status_flag_bits_are_not_error_codes():
+    """The flag bit lies above the error-code mask, and every error code
+    fits inside it."""
+    from paper_1505_04650_gb300 import _lib as L
+    assert L.CNMF_STATUS_NEGATIVE_A & L.CNMF_STATUS_CODE_MASK == 0
+    for code in (L.CNMF_E_INVALID_ARG, L.CNMF_E_WORKSPACE, L.CNMF_E_CUDA,
+                 L.CNMF_E_CHOLESKY, L.CNMF_E_NONFINITE, L.CNMF_E_TIMEOUT):
+        assert code & ~L.CNMF_STATUS_CODE_MASK == 0
+    h = open(os.path.join(ROOT, "include", "cnmf.h")).read()
+    assert "#define CNMF_STATUS_NEGATIVE_A 0x40000000" in h
+    assert "#define CNMF_STATUS_CODE_MASK 0x0000FFFF" in h
