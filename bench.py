@@ -219,6 +219,9 @@ TRAFFIC = {
     # profiles/k_tc_prod_f32_m20000_n10000_d30.md: A X 805.23 + 2.25 MB,
     # A^T Y 868.03 + 4.13 MB; one unit = one pass (both products)
     "k_tc_prod": {"bytes_per_unit": 1679.634432e6, "sha": "d74ba8dadf2e3d3d"},
+    # profiles/k_fused_pass_f32_m20000_n10000_d30.md: 812.32 MB read +
+    # 6.51 MB written by one two-sided pass (152 CTAs)
+    "k_fused_pass": {"bytes_per_unit": 818.831104e6, "sha": "1c8dd4068a2d9931"},
 }
 
 
@@ -242,6 +245,33 @@ def _traffic(kernel, units):
     return t["bytes_per_unit"] * units
 
 
+# ADMM launches in flight at once in the pipelined steps, and the SMs of
+# each (the compression stream gets the rest); see admm_split
+ADMM_STREAMS = 1
+
+
+def admm_split(nsm: int, nfs: int, admm_ctas: int = 0):
+    """(SMs per ADMM stream, SMs of the compression stream) for `nfs` ADMM
+    launches in flight beside one compression stream.  Measured on the
+    bench workload (factorizations/s): one ADMM stream on 76 / 92 / 104 /
+    116 SMs gives 111 / 115 / 122 / 113 -- past ~100 SMs the ADMM gains
+    nothing and the compression beside it loses; two streams of 48 / 54 /
+    60 SMs give 92 / 99 / 98 and three of 36 / 40 give 99 / 94, because
+    below ~70 CTAs the rows no longer stay in shared memory and a sweep
+    takes ~40 us.  Default: one stream on 104 of 152 SMs.
+    if admm_ctas > 0:
+        cap = admm_ctas
+    elif nfs == 1:
+        cap = nsm * 104 // 152
+    else:
+        cap = (nsm - nsm // 3) // nfs
+    cap_c = nsm - nfs * cap
+    if cap < 1 or cap_c < 8:
+        raise ValueError(f"{nfs} ADMM streams of {cap} SMs leave {cap_c} "
+                         f"of {nsm} SMs for the compression")
+    return cap, cap_c
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,8 +285,12 @@ def main(argv=None):
                     help="skip the served-stream measurement")
     ap.add_argument("--serving-requests", type=int, default=4096)
     ap.add_argument("--admm-ctas", type=int, default=0,
-                    help="SMs for the ADMM stream of the pipelined steps "
-                         "(the compression stream gets the rest; 0: half)")
+                    help="SMs for each ADMM stream of the pipelined steps "
+                         "(the compression stream gets the rest; 0: the "
+                         "default split)")
+    ap.add_argument("--admm-streams", type=int, default=ADMM_STREAMS,
+                    help="ADMM launches in flight at once in the pipelined "
+                         "steps (one stream each)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the wide-SNMF and mixed-precision lines")
     ap.add_argument("--cpu-sample-only", type=int, default=0,
@@ -311,38 +345,51 @@ def main(argv=None):
     # ADMM sweeps).  Consecutive steps are independent problems, so they are
     # pipelined on two streams: the compression of step k + 1 runs beside
     # the ADMM sweeps of step k, each call's grids capped at its share of
-    # the SMs (cnmf_set_thread_cta_limit; --admm-ctas, default half).  The ADMM is latency-bound (every CTA
-    # repeats the small algebra), so half the SMs slow it far less than
-    # they speed up the compression running beside it.
+    # the SMs (cnmf_set_thread_cta_limit; --admm-ctas, --admm-streams;
+    # default: the ADMM on 104 of 152 SMs, see admm_split).  The ADMM is
+    # latency-bound (every CTA repeats the small algebra), so fewer SMs slow
+    # it far less than they speed up the compression running beside it.
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    cap = args.admm_ctas if 0 < args.admm_ctas < nsm else nsm // 2
-    cap_c = nsm - cap                    # the compression stream's SMs
+    nfs = max(1, args.admm_streams)
+    cap, cap_c = admm_split(nsm, nfs, args.admm_ctas)
     sF = stream                          # ADMM sweeps
     sC = torch.cuda.Stream(dev)          # compressions
-    U = U0.clone()
-    Vt = Vt0.clone()
+    sFs = [sF] + [torch.cuda.Stream(dev) for _ in range(nfs - 1)]
+    Us = [U0.clone() for _ in range(nfs)]
+    Vts = [Vt0.clone() for _ in range(nfs)]
+    ws_fs = [ws_f] + [torch.empty_like(ws_f) for _ in range(nfs - 1)]
+    U, Vt = Us[0], Vts[0]
 
-    def pipe_step(fa=None):
+    def pipe_step(i, fa=None):
+        j = i % nfs
+        sf = sFs[j]
         cn.set_thread_cta_limit(cap_c)
         with torch.cuda.stream(sC):
             L, Rt, At, _ = cn.cnmf_compress(A, r, d, q, SEEDS["sketch"],
                                             status=st, ws=ws_c)
             ev = torch.cuda.Event()
             ev.record(sC)
-        sF.wait_event(ev)
+        sf.wait_event(ev)
         for t in (L, Rt, At):
-            t.record_stream(sF)
-        U.copy_(U0)
-        Vt.copy_(Vt0)
-        cn.set_thread_cta_limit(cap)
-        if fa is not None:
-            fa[0].record(sF)
-        cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
-        if fa is not None:
-            fa[1].record(sF)
+            t.record_stream(sf)
+        with torch.cuda.stream(sf):
+            Us[j].copy_(U0)
+            Vts[j].copy_(Vt0)
+            cn.set_thread_cta_limit(cap)
+            if fa is not None:
+                fa[0].record(sf)
+            cn.cnmf_factor(L, Rt, At, Us[j], Vts[j], lam, lam, iters,
+                           status=st, ws=ws_fs[j])
+            if fa is not None:
+                fa[1].record(sf)
 
-    for _ in range(max(args.warmup, 3)):
-        pipe_step()
+    def join_all():
+        for o in sFs[1:]:
+            sF.wait_stream(o)
+        sF.wait_stream(sC)
+
+    for i in range(max(args.warmup, 3)):
+        pipe_step(i)
     torch.cuda.synchronize()
     cn.raise_on_status(st, "bench warm-up")
 
@@ -354,10 +401,11 @@ def main(argv=None):
            for _ in range(args.steps)]
     with Clocks(local) as clk:
         ev0.record(sC)
-        sF.wait_event(ev0)
+        for o in sFs:
+            o.wait_event(ev0)
         for k in range(args.steps):
-            pipe_step(fas[k])
-        sF.wait_stream(sC)
+            pipe_step(k, fas[k])
+        join_all()
         ev1.record(sF)
         torch.cuda.synchronize()
     if world > 1:
@@ -469,14 +517,17 @@ def main(argv=None):
                    "q": q, "admm_iters": iters, "lambda": lam,
                    "l2": "inputs larger than L2 (A = 800 MB)",
                    "parallelism": f"replicas{world}",
-                   "pipelining": f"two streams: the compression of step "
-                                 f"k + 1 ({cap_c} SMs) beside the ADMM "
-                                 f"sweeps of step k ({cap} of {nsm} SMs)"},
+                   "pipelining": f"compressions on one stream ({cap_c} "
+                                 f"SMs) beside the ADMM sweeps of the "
+                                 f"previous {nfs} step(s), each ADMM launch "
+                                 f"on its own stream ({cap} of {nsm} SMs "
+                                 f"each)"},
         "roofline": {"bound": "hbm", "achieved": admm_gbs,
                      "peak": peaks["hbm"], "unit": "GB/s",
                      "frac": admm_gbs / peaks["hbm"], "traffic": traffic,
                      "kernel": f"k_admm_fast ({iters} sweeps, one launch, "
-                               f"{cap} CTAs beside a compression)",
+                               f"{cap} CTAs, beside a compression and "
+                               f"{nfs - 1} other ADMM launch(es))",
                      "algorithmic_bytes": admm_bytes,
                      "peak_source": peaks["src"] + " (copy bandwidth)",
                      "note": "latency-bound: the small algebra (two r x r "
@@ -521,7 +572,8 @@ def main(argv=None):
     # ---- end to end through the public API with host buffers: every step
     # copies its A, U0, V0^T from pinned host memory and reads U, V^T back,
     # pipelined like the timed steps (compressions on one stream, ADMM
-    # sweeps on another, each capped at half of the SMs).  The copy of the
+    # sweeps on the ADMM streams, each capped at its share of the SMs).  The
+    # copy of the
     # next step's A (a copy stream, into the other of two device buffers)
     # starts as soon as the previous step's compression is done with that
     # buffer.  The step's own U0, V0^T are queued before it: behind the
@@ -529,8 +581,9 @@ def main(argv=None):
     A_pin = torch.from_numpy(A_h).pin_memory()
     U_pin = torch.from_numpy(U0_h).pin_memory()
     Vt_pin = torch.from_numpy(Vt0_h).pin_memory()
-    U_out = torch.empty_like(U_pin).pin_memory()
-    Vt_out = torch.empty_like(Vt_pin).pin_memory()
+    U_outs = [torch.empty_like(U_pin).pin_memory() for _ in range(nfs)]
+    Vt_outs = [torch.empty_like(Vt_pin).pin_memory() for _ in range(nfs)]
+    U_out, Vt_out = U_outs[0], Vt_outs[0]
     A_dev = [A, torch.empty_like(A)]
     cstream = torch.cuda.Stream(dev)
     ev_in = [torch.cuda.Event() for _ in range(2)]     # A of step k landed
@@ -545,8 +598,11 @@ def main(argv=None):
 
     def e2e_step(k):
         b = k % 2
-        U.copy_(U_pin, non_blocking=True)          # on sF
-        Vt.copy_(Vt_pin, non_blocking=True)
+        j = k % nfs
+        sf = sFs[j]
+        with torch.cuda.stream(sf):
+            Us[j].copy_(U_pin, non_blocking=True)
+            Vts[j].copy_(Vt_pin, non_blocking=True)
         cn.set_thread_cta_limit(cap_c)
         with torch.cuda.stream(sC):
             sC.wait_event(ev_in[b])
@@ -554,24 +610,26 @@ def main(argv=None):
                                             status=st, ws=ws_c)
             ev_done[b].record(sC)
         h2d(k + 1, ev_done[1 - b])      # buffer of step k - 1, now free
-        sF.wait_event(ev_done[b])
+        sf.wait_event(ev_done[b])
         for t in (L, Rt, At):
-            t.record_stream(sF)
-        cn.set_thread_cta_limit(cap)
-        cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, iters, status=st, ws=ws_f)
-        U_out.copy_(U, non_blocking=True)
-        Vt_out.copy_(Vt, non_blocking=True)
+            t.record_stream(sf)
+        with torch.cuda.stream(sf):
+            cn.set_thread_cta_limit(cap)
+            cn.cnmf_factor(L, Rt, At, Us[j], Vts[j], lam, lam, iters,
+                           status=st, ws=ws_fs[j])
+            U_outs[j].copy_(Us[j], non_blocking=True)
+            Vt_outs[j].copy_(Vts[j], non_blocking=True)
 
     h2d(0, None)
     e2e_step(0)
     torch.cuda.synchronize()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ee0.record(sF)
-    sC.wait_event(ee0)
-    cstream.wait_event(ee0)
+    for o in sFs[1:] + [sC, cstream]:
+        o.wait_event(ee0)
     for k in range(1, args.steps + 1):
         e2e_step(k)
-    sF.wait_stream(sC)
+    join_all()
     sF.wait_stream(cstream)            # the last copy ends inside the region
     ee1.record(sF)
     torch.cuda.synchronize()
