@@ -258,7 +258,7 @@ def admm_split(nsm: int, nfs: int, admm_ctas: int = 0):
     nothing and the compression beside it loses; two streams of 48 / 54 /
     60 SMs give 92 / 99 / 98 and three of 36 / 40 give 99 / 94, because
     below ~70 CTAs the rows no longer stay in shared memory and a sweep
-    takes ~40 us.  Default: one stream on 104 of 152 SMs.
+    takes ~40 us.  Default: one stream on 104 of 152 SMs."""
     if admm_ctas > 0:
         cap = admm_ctas
     elif nfs == 1:
