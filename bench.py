@@ -160,6 +160,15 @@ def cpu_oracle_snmf_wide():
     return secs, sorted(int(k) for k in K) == sorted(int(k) for k in planted)
 
 
+def bench_config(world: int) -> dict:
+    """The workload both arms measure (the same dict in both JSON lines;
+    run-specific settings such as the penalty go under "run")."""
+    return {"workload": WORKLOAD, "m": CFG["m"], "n": CFG["n"], "r": CFG["r"],
+            "d": CFG["d"], "q": CFG["q"], "admm_iters": CFG["iters"],
+            "l2": "inputs larger than L2 (A = 800 MB)",
+            "parallelism": f"replicas{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -181,10 +190,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1000.0 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": CFG["m"], "n": CFG["n"],
-                   "r": CFG["r"], "d": CFG["d"], "q": CFG["q"],
-                   "admm_iters": CFG["iters"],
-                   "l2": "inputs larger than L2"},
+        "config": bench_config(int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": "factorizations/s",
                          "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "factorizations/s",
@@ -513,15 +519,12 @@ def main(argv=None):
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": m, "n": n, "r": r, "d": d,
-                   "q": q, "admm_iters": iters, "lambda": lam,
-                   "l2": "inputs larger than L2 (A = 800 MB)",
-                   "parallelism": f"replicas{world}",
-                   "pipelining": f"compressions on one stream ({cap_c} "
-                                 f"SMs) beside the ADMM sweeps of the "
-                                 f"previous {nfs} step(s), each ADMM launch "
-                                 f"on its own stream ({cap} of {nsm} SMs "
-                                 f"each)"},
+        "config": bench_config(world),
+        "run": {"lambda": lam,
+                "pipelining": f"compressions on one stream ({cap_c} SMs) "
+                              f"beside the ADMM sweeps of the previous "
+                              f"{nfs} step(s), each ADMM launch on its own "
+                              f"stream ({cap} of {nsm} SMs each)"},
         "roofline": {"bound": "hbm", "achieved": admm_gbs,
                      "peak": peaks["hbm"], "unit": "GB/s",
                      "frac": admm_gbs / peaks["hbm"], "traffic": traffic,

@@ -23,7 +23,13 @@ def test_reference_arm_json_line():
     assert line["value"] > 0 and line["unit"] == "factorizations/s"
     assert line["higher_is_better"] is True
     assert line["config"]["workload"].startswith("cnmf_m20000_n10000")
+    # the same config dict as this library's arm prints (run settings such
+    # as the penalty live under "run" there)
+    import bench
+    assert line["config"] == bench.bench_config(1)
+    assert "lambda" not in line["config"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     e2e = line["e2e"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
