@@ -214,11 +214,17 @@ cnmf_status cnmf_compress(const void* A, cnmf_dtype a_type, int64_t m,
  *               memory: page-locked for the full copy rate, pageable works
  *               slower; a device pointer works too).  It must stay valid
  *               and unchanged until the stream has finished the call.
- *   block_rows  rows per block (>= 1): each block is copied into one
- *               device buffer of block_rows x n and goes through the same
- *               product kernels as cnmf_compress (the fused one-read pass
- *               for FP32 / BF16 and d <= 32); the blocks' shares of A^T Y
- *               are added in block order.
+ *   block_rows  rows per block (>= 1): each block is copied into one of
+ *               two device buffers of block_rows x n and goes through the
+ *               same product kernels as cnmf_compress (the fused one-read
+ *               pass for FP32 / BF16 and d <= 32); the blocks' shares of
+ *               A^T Y are added in block order.  The copies run on a copy
+ *               stream of the library's own (one non-blocking stream and
+ *               five events per host thread and device, created on the
+ *               thread's first call on that device and kept until exit),
+ *               so the copy of block k + 1 overlaps block k's products;
+ *               events order the two streams, and the call still returns
+ *               with all its work ordered on `stream`.
  *   Everything else as cnmf_compress: the m x d and n x d panels, their
  *   CholeskyQR2 (whose Gram matrices are the sums over row blocks -- the
  *   one central reduction TSQR provides in the paper) and A-tilde stay in

@@ -235,59 +235,144 @@ static cnmf_status launch_acc(void* x, const void* y, int64_t count,
 // orthonormalisation (CholeskyQR2: its Gram matrices are sums over row
 // blocks of the resident panels, the one central reduction that TSQR plays
 // in the paper's out-of-core setting) and A-tilde stay in device memory.
+// The copy lane of the out-of-core passes: one non-blocking stream and
+// five events per host thread and device, created on the thread's first
+// out-of-core call on that device and kept until exit.  Block copies run on
+// it, so the copy of block k + 1 overlaps the products of block k on the
+// caller's stream; events order the two (no host synchronisation).
+struct CopyLane {
+  bool ok = false;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr},
+              freed[2] = {nullptr, nullptr};
+};
+constexpr int LANE_DEVS = 16;
+
+static CopyLane* copy_lane() {
+  static thread_local CopyLane lanes[LANE_DEVS];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= LANE_DEVS) {
+    (void)cudaGetLastError();
+    return nullptr;   // the caller's stream alone (no overlap)
+  }
+  CopyLane& l = lanes[dev];
+  if (!l.ok) {
+    const unsigned f = cudaEventDisableTiming;
+    bool good =
+        cudaStreamCreateWithFlags(&l.cs, cudaStreamNonBlocking) == cudaSuccess;
+    good = good && cudaEventCreateWithFlags(&l.start, f) == cudaSuccess;
+    for (int i = 0; i < 2 && good; ++i)
+      good = cudaEventCreateWithFlags(&l.copied[i], f) == cudaSuccess &&
+             cudaEventCreateWithFlags(&l.freed[i], f) == cudaSuccess;
+    if (!good) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    l.ok = true;
+  }
+  return &l;
+}
+
+// A in host memory: each pass copies A in row blocks into one of two device
+// buffers and runs the block through the same product kernels; the blocks'
+// shares of A^T Y are added in block order.  With a copy lane, block k + 1
+// is copied (lane stream) while block k's products run (caller's stream);
+// block k + 2 reuses block k's buffer once its products are done.
 struct HostSource : PassSource {
   const void* A;
   cnmf_dtype a_type;
   int64_t m, n, lda;
   int d;
   int64_t rows_blk;
-  void* blk;         // rows_blk x ldb, a_type
+  void* blk[2];      // rows_blk x ldb each, a_type
   int64_t ldb;
   void* znb;         // n x KP, the block's share of A^T Y
   const CompressLayout* lay;
   int32_t* status;
   cudaStream_t s;
+  CopyLane* lane;    // null: copies on s, one after the other
 
   size_t es() const {
     return a_type == CNMF_F64 ? 8 : (a_type == CNMF_F32 ? 4 : 2);
   }
-  cnmf_status copy(int64_t i0, int64_t mb) {
+  // copy block k (rows i0 .. i0 + mb) into its buffer
+  cnmf_status copy(int64_t k, int64_t i0, int64_t mb) {
     const size_t e = es();
-    CNMF_CUDA(cudaMemcpy2DAsync(blk, (size_t)ldb * e,
+    const int b = (int)(k & 1);
+    cudaStream_t cs = lane ? lane->cs : s;
+    if (lane && k >= 2) CNMF_CUDA(cudaStreamWaitEvent(cs, lane->freed[b], 0));
+    CNMF_CUDA(cudaMemcpy2DAsync(blk[b], (size_t)ldb * e,
                                 (const char*)A + (size_t)i0 * lda * e,
                                 (size_t)lda * e, (size_t)n * e, (size_t)mb,
-                                cudaMemcpyDefault, s));
+                                cudaMemcpyDefault, cs));
+    if (lane) CNMF_CUDA(cudaEventRecord(lane->copied[b], cs));
     return CNMF_OK;
   }
-  DeviceSource block(int64_t mb) const {
+  // block k's products wait for its copy (enqueued on s just before them,
+  // after the copy of block k + 1 has been issued)
+  cnmf_status arrived(int64_t k) {
+    if (lane) CNMF_CUDA(cudaStreamWaitEvent(s, lane->copied[k & 1], 0));
+    return CNMF_OK;
+  }
+  // the lane starts after everything already on s (the buffers' last
+  // readers, the panels of the pass before)
+  cnmf_status begin() {
+    if (!lane) return CNMF_OK;
+    CNMF_CUDA(cudaEventRecord(lane->start, s));
+    CNMF_CUDA(cudaStreamWaitEvent(lane->cs, lane->start, 0));
+    return CNMF_OK;
+  }
+  cnmf_status done(int64_t k) {
+    if (lane) CNMF_CUDA(cudaEventRecord(lane->freed[k & 1], s));
+    return CNMF_OK;
+  }
+  DeviceSource block(int64_t k, int64_t mb) const {
     DeviceSource b;
-    b.A = blk; b.a_type = a_type; b.m = mb; b.n = n; b.lda = ldb; b.d = d;
-    b.lay = lay; b.status = status; b.s = s;
+    b.A = blk[k & 1]; b.a_type = a_type; b.m = mb; b.n = n; b.lda = ldb;
+    b.d = d; b.lay = lay; b.status = status; b.s = s;
     return b;
   }
   cnmf_status both(const void* X, int64_t ldx, const void* Y, int64_t ldy,
                    void* zm, void* zn) override {
     const size_t w = wbytes(work_type(a_type));
     const int KP = lay->KP;
-    for (int64_t i0 = 0; i0 < m; i0 += rows_blk) {
+    CNMF_TRY(begin());
+    const int64_t nblk = ceil_div(m, rows_blk);
+    // the first copy goes out ahead; then the copy of block k + 1 is issued
+    // before block k's products
+    CNMF_TRY(copy(0, 0, std::min(rows_blk, m)));
+    for (int64_t k = 0; k < nblk; ++k) {
+      const int64_t i0 = k * rows_blk;
       const int64_t mb = std::min(rows_blk, m - i0);
-      CNMF_TRY(copy(i0, mb));
-      DeviceSource b = block(mb);
+      if (k + 1 < nblk)
+        CNMF_TRY(copy(k + 1, i0 + rows_blk,
+                      std::min(rows_blk, m - i0 - rows_blk)));
+      CNMF_TRY(arrived(k));
+      DeviceSource b = block(k, mb);
       CNMF_TRY(b.both(X, ldx, (const char*)Y + (size_t)i0 * ldy * w, ldy,
                       (char*)zm + (size_t)i0 * KP * w, znb));
       CNMF_TRY(launch_acc(zn, znb, n * (int64_t)KP, i0 == 0,
                           work_type(a_type), s));
+      CNMF_TRY(done(k));
     }
     return CNMF_OK;
   }
   cnmf_status left(const void* X, int64_t ldx, void* zm) override {
     const size_t w = wbytes(work_type(a_type));
     const int KP = lay->KP;
-    for (int64_t i0 = 0; i0 < m; i0 += rows_blk) {
+    CNMF_TRY(begin());
+    const int64_t nblk = ceil_div(m, rows_blk);
+    CNMF_TRY(copy(0, 0, std::min(rows_blk, m)));
+    for (int64_t k = 0; k < nblk; ++k) {
+      const int64_t i0 = k * rows_blk;
       const int64_t mb = std::min(rows_blk, m - i0);
-      CNMF_TRY(copy(i0, mb));
-      DeviceSource b = block(mb);
+      if (k + 1 < nblk)
+        CNMF_TRY(copy(k + 1, i0 + rows_blk,
+                      std::min(rows_blk, m - i0 - rows_blk)));
+      CNMF_TRY(arrived(k));
+      DeviceSource b = block(k, mb);
       CNMF_TRY(b.left(X, ldx, (char*)zm + (size_t)i0 * KP * w));
+      CNMF_TRY(done(k));
     }
     return CNMF_OK;
   }
@@ -296,7 +381,7 @@ struct HostSource : PassSource {
 struct HostLayout {
   CompressLayout lay;
   int64_t rows_blk, ldb;
-  void *blk, *znb;
+  void *blk[2], *znb;
   size_t bytes;
 };
 
@@ -308,7 +393,8 @@ static HostLayout host_layout(void* ws, int64_t m, int64_t n, int d,
   const size_t e = a_type == CNMF_F64 ? 8 : (a_type == CNMF_F32 ? 4 : 2);
   H.ldb = (n + 7) / 8 * 8;
   Carve cv(ws ? (char*)ws + H.lay.bytes : nullptr, SIZE_MAX);
-  H.blk = cv.take<char>((size_t)H.rows_blk * H.ldb * e);
+  H.blk[0] = cv.take<char>((size_t)H.rows_blk * H.ldb * e);
+  H.blk[1] = cv.take<char>((size_t)H.rows_blk * H.ldb * e);
   H.znb = cv.take<char>((size_t)n * H.lay.KP * wbytes(work_type(a_type)));
   H.bytes = H.lay.bytes + cv.off;
   return H;
@@ -448,8 +534,9 @@ extern "C" cnmf_status cnmf_compress_host(const void* A, cnmf_dtype a_type,
   cudaStream_t s = (cudaStream_t)stream;
   HostSource src;
   src.A = A; src.a_type = a_type; src.m = m; src.n = n; src.lda = lda;
-  src.d = d; src.rows_blk = H.rows_blk; src.blk = H.blk; src.ldb = H.ldb;
-  src.znb = H.znb; src.lay = &H.lay; src.status = dev_status; src.s = s;
+  src.d = d; src.rows_blk = H.rows_blk; src.blk[0] = H.blk[0];
+  src.blk[1] = H.blk[1]; src.ldb = H.ldb; src.znb = H.znb; src.lay = &H.lay;
+  src.status = dev_status; src.s = s; src.lane = copy_lane();
   return compress_passes(src, a_type, m, n, r, d, q, seed, Omega, Psi, L, Rt,
                          Atilde, H.lay, dev_status, s);
 }
