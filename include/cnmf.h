@@ -496,6 +496,36 @@ cnmf_status cnmf_check_nonnegative(const void* A, cnmf_dtype a_type,
                                    int32_t* dev_status, cnmf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * cnmf_residual_batched: cnmf_residual for many problems in one launch (the
+ * accuracy checks of a served batch).  Item i: out2[2 i] = ||A - U V||_F^2,
+ * out2[2 i + 1] = ||A||_F^2 (FP64, device), one read of its A.
+ *   items   DEVICE array of nitems cnmf_residual_item (below); all items
+ *           share a_type and w_type (as in cnmf_residual); 1 <= r <= max_r
+ *           <= 128 per item.  An item that breaks these rules gets NaN
+ *           pairs and CNMF_E_INVALID_ARG in *dev_status (optional).
+ *   ctas_per_item  CTAs that split each item's 64 x 64 tiles (1..1024);
+ *           each item's sums run in CTA order, so results do not depend on
+ *           timing (they may differ from cnmf_residual's in the last bits:
+ *           another split of the same sums).
+ *   ws      cnmf_residual_batched_workspace(nitems, ctas_per_item) bytes.
+ * The launch reads `items` when it runs.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  const void* A;   /* m x n, pitch lda */
+  const void* U;   /* m x r */
+  const void* Vt;  /* n x r */
+  int64_t m, n, lda;
+  int32_t r, reserved;
+} cnmf_residual_item;
+size_t cnmf_residual_batched_workspace(int32_t nitems, int32_t ctas_per_item);
+cnmf_status cnmf_residual_batched(const cnmf_residual_item* items,
+                                  int32_t nitems, cnmf_dtype a_type,
+                                  cnmf_dtype w_type, int32_t max_r,
+                                  int32_t ctas_per_item, double* out2,
+                                  void* ws, size_t ws_bytes,
+                                  int32_t* dev_status, cnmf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * cnmf_residual_noalloc: the same result as cnmf_residual, for callers that
  * cannot allocate device memory -- for example a plugin whose host
  * application owns every device allocation, code running while another

@@ -512,6 +512,41 @@ def cnmf_residual(A: torch.Tensor, U: torch.Tensor, Vt: torch.Tensor,
     return out
 
 
+def residual_item_bytes(A: torch.Tensor, U: torch.Tensor,
+                        Vt: torch.Tensor) -> bytes:
+    """Host image of one cnmf_residual_item (for cnmf_residual_batched)."""
+    m, n, lda = _mat(A)
+    r = U.shape[1]
+    w = _wdtype(A.dtype)
+    _dense(U, (m, r), w, "U")
+    _dense(Vt, (n, r), w, "Vt")
+    return bytes(_lib.ResidualItem(A.data_ptr(), U.data_ptr(), Vt.data_ptr(),
+                                   m, n, lda, r, 0))
+
+
+def cnmf_residual_batched(items_dev: torch.Tensor, nitems: int,
+                          a_dtype: torch.dtype, max_r: int,
+                          ctas_per_item: int = 8,
+                          out: torch.Tensor | None = None, ws=None,
+                          status: torch.Tensor | None = None) -> torch.Tensor:
+    """(nitems, 2) device FP64 pairs (||A - U V||^2, ||A||^2), one launch for
+    all items; items_dev holds nitems cnmf_residual_item records (device
+    memory, e.g. copied from residual_item_bytes images)."""
+    dev = items_dev.device
+    lb = lib()
+    if out is None:
+        out = torch.empty(nitems, 2, dtype=torch.float64, device=dev)
+    nb = lb.cnmf_residual_batched_workspace(nitems, ctas_per_item)
+    if ws is None or ws.numel() < nb:
+        ws = _ws(nb, dev)
+    _check(lb.cnmf_residual_batched(_ptr(items_dev), nitems, _DT[a_dtype],
+                                    _DT[_wdtype(a_dtype)], max_r,
+                                    ctas_per_item, _ptr(out), _ptr(ws),
+                                    ws.numel(), _ptr(status), _stream(dev)),
+           "cnmf_residual_batched")
+    return out
+
+
 # --------------------------------------------------------------------------
 class BatchProblem:
     """Device buffers of one problem for cnmf_factor_batched (FP32).
@@ -546,6 +581,16 @@ class BatchProblem:
                               self.m, self.n, self.r, self.d, self.lam,
                               self.phi, self.xi,
                               _lib.CNMF_BATCH_FRESH if self.fresh else 0, 0)
+
+    def item_bytes(self) -> bytes:
+        """Host image of item(), kept until the penalties or the FRESH flag
+        change (building the ctypes record costs more than a round's GPU
+        work when many problems are in flight)."""
+        key = (self.fresh, self.lam, self.phi, self.xi)
+        if getattr(self, "_item_key", None) != key:
+            self._item_bytes = bytes(self.item())
+            self._item_key = key
+        return self._item_bytes
 
 
 def pack_items(problems) -> bytes:

@@ -43,6 +43,13 @@ class BatchItem(C.Structure):
                 ("reserved", c_int32)]
 
 
+class ResidualItem(C.Structure):
+    """cnmf_residual_item (include/cnmf.h)."""
+    _fields_ = [("A", c_void_p), ("U", c_void_p), ("Vt", c_void_p),
+                ("m", c_int64), ("n", c_int64), ("lda", c_int64),
+                ("r", c_int32), ("reserved", c_int32)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "cnmf_status_string": (C.c_char_p, [c_int32]),
@@ -121,6 +128,10 @@ SIGNATURES = {
     "cnmf_residual": (c_int32, [c_void_p, c_int32, c_int64, c_int64, c_int64,
                                 c_void_p, c_void_p, c_int32, c_int32,
                                 c_void_p, c_void_p, c_size_t, c_void_p]),
+    "cnmf_residual_batched_workspace": (c_size_t, [c_int32, c_int32]),
+    "cnmf_residual_batched": (c_int32, [c_void_p, c_int32, c_int32, c_int32,
+                                        c_int32, c_int32, c_void_p, c_void_p,
+                                        c_size_t, c_void_p, c_void_p]),
     "cnmf_check_nonnegative": (c_int32, [c_void_p, c_int32, c_int64,
                                          c_int64, c_int64, c_void_p,
                                          c_void_p]),

@@ -15,11 +15,15 @@ namespace cnmf {
 constexpr int RS_NT = 256;
 constexpr int RS_T = 64;
 
+// The tiles cta, cta + ncta, ... of one problem; the CTA's FP64 pair goes
+// to part[0], part[1].
 template <typename TA, typename W>
-__global__ void __launch_bounds__(RS_NT)
-    k_residual(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda,
-               const W* __restrict__ U, const W* __restrict__ Vt, int r,
-               double* __restrict__ part) {
+__device__ __forceinline__ void res_tiles(const TA* __restrict__ A, int64_t m,
+                                          int64_t n, int64_t lda,
+                                          const W* __restrict__ U,
+                                          const W* __restrict__ Vt, int r,
+                                          int64_t cta, int64_t ncta,
+                                          double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int RPAD = r + 1;
   W* Us = reinterpret_cast<W*>(smem);   // 64 x (r+1)
@@ -28,7 +32,7 @@ __global__ void __launch_bounds__(RS_NT)
   const int64_t tm = ceil_div(m, RS_T), tn = ceil_div(n, RS_T);
   const int64_t ntiles = tm * tn;
   double e2 = 0.0, a2 = 0.0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int64_t t = cta; t < ntiles; t += ncta) {
     const int64_t i0 = (t / tn) * RS_T, j0 = (t % tn) * RS_T;
     __syncthreads();
     for (int e = threadIdx.x; e < RS_T * r; e += RS_NT) {
@@ -84,9 +88,73 @@ __global__ void __launch_bounds__(RS_NT)
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = re[0];
-    part[2 * blockIdx.x + 1] = ra[0];
+    part[0] = re[0];
+    part[1] = ra[0];
   }
+}
+
+template <typename TA, typename W>
+__global__ void __launch_bounds__(RS_NT)
+    k_residual(const TA* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+               const W* __restrict__ U, const W* __restrict__ Vt, int r,
+               double* __restrict__ part) {
+  res_tiles<TA, W>(A, m, n, lda, U, Vt, r, blockIdx.x, gridDim.x,
+                   part + 2 * blockIdx.x);
+}
+
+// Many problems in one launch: blockIdx.y is the item, blockIdx.x one of
+// its gridDim.x CTAs.  An item that does not fit the launch (r above max_r,
+// bad sizes) reports CNMF_E_INVALID_ARG and gets NaN pairs.
+template <typename TA, typename W>
+__global__ void __launch_bounds__(RS_NT)
+    k_residual_batched(const cnmf_residual_item* __restrict__ items,
+                       int max_r, double* __restrict__ part,
+                       int32_t* __restrict__ status) {
+  const cnmf_residual_item it = items[blockIdx.y];
+  double* p = part + 2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
+  const bool ok = it.A && it.U && it.Vt && it.m >= 1 && it.n >= 1 &&
+                  it.lda >= it.n && it.r >= 1 && it.r <= max_r;
+  if (!ok) {   // uniform per block
+    if (threadIdx.x == 0) {
+      p[0] = p[1] = __longlong_as_double(0x7ff8000000000000ll);
+      if (blockIdx.x == 0) set_status(status, CNMF_E_INVALID_ARG);
+    }
+    return;
+  }
+  res_tiles<TA, W>((const TA*)it.A, it.m, it.n, it.lda, (const W*)it.U,
+                   (const W*)it.Vt, it.r, blockIdx.x, gridDim.x, p);
+}
+
+// out2[2 i], out2[2 i + 1] = the sums of item i's G pairs, in CTA order
+__global__ void k_residual_sum_batched(const double* __restrict__ part, int G,
+                                       int nitems, double* __restrict__ out2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nitems) return;
+  double e = 0.0, a = 0.0;
+  for (int g = 0; g < G; ++g) {
+    e += part[2 * ((size_t)i * G + g)];
+    a += part[2 * ((size_t)i * G + g) + 1];
+  }
+  out2[2 * i] = e;
+  out2[2 * i + 1] = a;
+}
+
+template <typename TA, typename W>
+static cnmf_status run_res_batched(const cnmf_residual_item* items, int nitems,
+                                   int max_r, int G, double* out2, void* ws,
+                                   int32_t* status, cudaStream_t s) {
+  const size_t smem = sizeof(W) * 2 * RS_T * (max_r + 1);
+  if (!ensure_max_smem((const void*)k_residual_batched<TA, W>,
+                       sizeof(W) * 2 * RS_T * 129))
+    return CNMF_E_INVALID_ARG;
+  double* part = (double*)ws;
+  k_residual_batched<TA, W><<<dim3(G, nitems), RS_NT, smem, s>>>(
+      items, max_r, part, status);
+  CNMF_CHECK_LAUNCH();
+  k_residual_sum_batched<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(
+      part, G, nitems, out2);
+  CNMF_CHECK_LAUNCH();
+  return CNMF_OK;
 }
 
 __global__ void k_residual_sum(const double* __restrict__ part, int G,
@@ -178,6 +246,36 @@ extern "C" cnmf_status cnmf_residual_noalloc(const void* A, cnmf_dtype a_type,
   if (a_type == CNMF_F32)
     return run_res<float, float>(A, m, n, lda, U, Vt, r, out2, scratch, s);
   return run_res<bf16, float>(A, m, n, lda, U, Vt, r, out2, scratch, s);
+}
+
+extern "C" size_t cnmf_residual_batched_workspace(int32_t nitems,
+                                                  int32_t ctas_per_item) {
+  if (nitems < 1 || ctas_per_item < 1 || ctas_per_item > 1024) return 0;
+  return (size_t)2 * sizeof(double) * nitems * ctas_per_item + 256;
+}
+
+extern "C" cnmf_status cnmf_residual_batched(
+    const cnmf_residual_item* items, int32_t nitems, cnmf_dtype a_type,
+    cnmf_dtype w_type, int32_t max_r, int32_t ctas_per_item, double* out2,
+    void* ws, size_t ws_bytes, int32_t* dev_status, cnmf_stream_t stream) {
+  if (!items || !out2 || !ws || nitems < 1 || nitems > 65535 || max_r < 1 ||
+      max_r > 128 || ctas_per_item < 1 || ctas_per_item > 1024 ||
+      (a_type != CNMF_F64 && a_type != CNMF_F32 && a_type != CNMF_BF16) ||
+      (w_type != CNMF_F64 && w_type != CNMF_F32) ||
+      (a_type == CNMF_F64) != (w_type == CNMF_F64))
+    return CNMF_E_INVALID_ARG;
+  if (ws_bytes < cnmf_residual_batched_workspace(nitems, ctas_per_item))
+    return CNMF_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a_type == CNMF_F64)
+    return run_res_batched<double, double>(items, nitems, max_r,
+                                           ctas_per_item, out2, ws,
+                                           dev_status, s);
+  if (a_type == CNMF_F32)
+    return run_res_batched<float, float>(items, nitems, max_r, ctas_per_item,
+                                         out2, ws, dev_status, s);
+  return run_res_batched<bf16, float>(items, nitems, max_r, ctas_per_item,
+                                      out2, ws, dev_status, s);
 }
 
 extern "C" size_t cnmf_residual_workspace(int64_t m, int64_t n, int32_t r,

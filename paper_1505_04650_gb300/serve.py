@@ -45,7 +45,8 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import (BatchProblem, _lib, cnmf_compress, cnmf_residual, lib,
+from . import (BatchProblem, _lib, cnmf_compress, cnmf_residual,
+               cnmf_residual_batched, lib, residual_item_bytes,
                raise_on_status)
 from .autotune import Autotuner
 
@@ -82,6 +83,7 @@ class Request:
     fut: concurrent.futures.Future | None = None
     U: torch.Tensor | None = None
     Vt: torch.Tensor | None = None
+    res_item: bytes = b""       # cnmf_residual_item record of the checks
 
 
 def make_workload(nreq: int, rate: float, seed: int = 0, m_range=(200, 4000),
@@ -129,7 +131,7 @@ def request_bytes(rq: Request) -> int:
 
 class Server:
     def __init__(self, hbm_budget: float = 40e9, max_slots: int = 512,
-                 sweeps_per_round: int = 10, compress_streams: int = 4,
+                 sweeps_per_round: int = 20, compress_streams: int = 4,
                  tuner: Autotuner | None = None, use_graphs: bool = True,
                  stop_at_target: bool = False, check_every: int = 20,
                  max_sweeps: int = 3000, penalty_scale: float = 0.3,
@@ -188,11 +190,22 @@ class Server:
 
     def _round(self, key, reqs: list[Request]):
         g = self._group(key)
-        arr = (_lib.BatchItem * self.max_slots)()
-        for i, rq in enumerate(reqs):
-            arr[i] = rq.problem.item()
-        g["host"].numpy()[:] = np.frombuffer(bytes(arr), dtype=np.uint8)
-        g["items"].copy_(g["host"], non_blocking=True)
+        # the device item array changes only when the group's members or a
+        # member's FRESH flag change; then it is rebuilt from each problem's
+        # cached host image (empty slots zero) and copied, once the previous
+        # copy out of the pinned staging buffer has finished
+        sig = [(id(rq), rq.problem.fresh) for rq in reqs]
+        if g.get("sig") != sig:
+            blob = b"".join(rq.problem.item_bytes() for rq in reqs)
+            if g.get("copy_ev") is not None:
+                g["copy_ev"].synchronize()
+            host = g["host"].numpy()
+            host[:len(blob)] = np.frombuffer(blob, dtype=np.uint8)
+            host[len(blob):] = 0
+            g["items"].copy_(g["host"], non_blocking=True)
+            g["copy_ev"] = torch.cuda.Event()
+            g["copy_ev"].record(torch.cuda.current_stream(self.dev))
+            g["sig"] = sig
         if not self.use_graphs:
             self._launch(key, g)
         else:
@@ -216,6 +229,39 @@ class Server:
         for rq in reqs:
             rq.problem.fresh = False
             rq.done_sweeps += self.S
+
+    def _res_buf(self, n: int) -> torch.Tensor:
+        """Device FP64 pairs for `n` residual checks, grown as needed."""
+        if getattr(self, "_res", None) is None or self._res.shape[0] < n:
+            self._res = torch.empty(max(n, 64), 2, dtype=torch.float64,
+                                    device=self.dev)
+        return self._res
+
+    def _check_batch(self, due: list[Request], res_all: torch.Tensor):
+        """The residuals of every request due for a check in one launch
+        (cnmf_residual_batched) on the main stream, into res_all[:len(due)].
+        The item records are staged in pinned memory (the previous check
+        round ended with a synchronisation, so the staging buffer is free)
+        and copied with the launch."""
+        blob = b"".join(rq.res_item for rq in due)
+        nb = len(blob)
+        if getattr(self, "_ri_host", None) is None or \
+                self._ri_host.numel() < nb:
+            cap = max(nb, 64 * C.sizeof(_lib.ResidualItem)) * 2
+            self._ri_host = torch.empty(cap, dtype=torch.uint8).pin_memory()
+            self._ri_dev = torch.empty(cap, dtype=torch.uint8,
+                                       device=self.dev)
+        self._ri_host.numpy()[:nb] = np.frombuffer(blob, dtype=np.uint8)
+        self._ri_dev[:nb].copy_(self._ri_host[:nb], non_blocking=True)
+        ctas = 8
+        wsb = self.lib.cnmf_residual_batched_workspace(len(due), ctas)
+        if getattr(self, "_rbws", None) is None or self._rbws.numel() < wsb:
+            self._rbws = torch.empty(2 * wsb, dtype=torch.uint8,
+                                     device=self.dev)
+        cnmf_residual_batched(self._ri_dev, len(due), torch.float32,
+                              max(rq.r for rq in due), ctas,
+                              out=res_all[:len(due)], ws=self._rbws,
+                              status=self.status)
 
     def prepare(self, requests: list[Request]):
         """Tune every size bucket the requests touch before serving."""
@@ -269,6 +315,9 @@ class Server:
                   pb.scratch, rq.A):
             t.record_stream(self.main)
         rq.t_compressed = now
+        # the record of this request's residual checks (its buffers stay in
+        # place until it is done)
+        rq.res_item = residual_item_bytes(rq.A, pb.U, pb.Vt)
         if self.stop_at_target:
             # the target's reference point, the residual of the rank-r
             # truncation of A-tilde (host SVD of the d x d copy), queued on
@@ -336,23 +385,29 @@ class Server:
                         self._round(key, reqs[i:i + self.max_slots])
                 rounds += 1
                 if self.stop_at_target:
-                    # residual of the requests due for a check
+                    # residual of the requests due for a check, all into
+                    # one device buffer and read back with one copy; a
+                    # round with nothing due (and no target pending) goes
+                    # on without waiting for the device
                     due = [rq for rq in running
                            if rq.done_sweeps % self.check_every == 0
                            or rq.done_sweeps >= self.max_sweeps]
-                    outs = [cnmf_residual(rq.A, rq.problem.U, rq.problem.Vt)
-                            for rq in due]
-                    self.main.synchronize()   # this round only
+                    newf = [rq for rq in running if rq.floor_res is not None]
+                    if not due and not newf:
+                        continue
+                    res_all = self._res_buf(len(due))
+                    if due:
+                        self._check_batch(due, res_all)
+                    self.main.synchronize()   # this round's checks
                     now = clock()
-                    for rq in running:
-                        if rq.floor_res is not None:
-                            e2, a2 = rq.floor_res.cpu().tolist()
-                            rq.floor = math.sqrt(e2 / a2)
-                            rq.tau = rq.floor + 1e-3
-                            rq.floor_res = None
+                    for rq in newf:
+                        e2, a2 = rq.floor_res.cpu().tolist()
+                        rq.floor = math.sqrt(e2 / a2)
+                        rq.tau = rq.floor + 1e-3
+                        rq.floor_res = None
+                    vals = res_all[:len(due)].cpu()
                     finished = []
-                    for rq, res in zip(due, outs):
-                        res = res.cpu()
+                    for rq, res in zip(due, vals):
                         e2, a2 = res.tolist()
                         if math.sqrt(e2 / a2) <= rq.tau or \
                                 rq.done_sweeps >= self.max_sweeps:
