@@ -966,7 +966,7 @@ def time_to_target(cn, A, U0, Vt0, ws_c, ws_f, st, stream, noiseless=False,
         e2, b2 = cn.cnmf_residual(A, U, Vt).cpu().tolist()
         return float(np.sqrt(e2 / b2))
 
-    scales = (0.1, 0.3, 1.0)
+    scales = (0.03, 0.1, 0.3, 1.0, 3.0)
     out = {"tau": tau, "floor_est": floor,
            "penalty_sweep": "lambda = phi = c ||M||_F / r, c in "
                             f"{list(scales)}, best per method"}
