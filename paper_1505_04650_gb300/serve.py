@@ -38,7 +38,9 @@ import collections
 import concurrent.futures
 import ctypes as C
 import math
+import contextlib
 import queue
+import threading
 import time
 from dataclasses import dataclass
 
@@ -129,6 +131,49 @@ def request_bytes(rq: Request) -> int:
     return b
 
 
+class _CaptureGate:
+    """Admission threads issue CUDA work together (shared); a CUDA-graph
+    capture on the serving thread runs alone (exclusive), so no other
+    thread's call (an allocation, a synchronising query, the autotuner's
+    timing) lands inside a capture and invalidates it.  A waiting capture
+    holds back new admissions; admissions never wait on the serving
+    thread, so the capture always gets its turn."""
+
+    def __init__(self):
+        self._c = threading.Condition()
+        self._shared = 0
+        self._excl = False
+        self._waiting = 0
+
+    @contextlib.contextmanager
+    def shared(self):
+        with self._c:
+            while self._excl or self._waiting:
+                self._c.wait()
+            self._shared += 1
+        try:
+            yield
+        finally:
+            with self._c:
+                self._shared -= 1
+                self._c.notify_all()
+
+    @contextlib.contextmanager
+    def exclusive(self):
+        with self._c:
+            self._waiting += 1
+            while self._excl or self._shared:
+                self._c.wait()
+            self._waiting -= 1
+            self._excl = True
+        try:
+            yield
+        finally:
+            with self._c:
+                self._excl = False
+                self._c.notify_all()
+
+
 class Server:
     def __init__(self, hbm_budget: float = 40e9, max_slots: int = 512,
                  sweeps_per_round: int = 20, compress_streams: int = 4,
@@ -166,6 +211,7 @@ class Server:
         torch.backends.cuda.matmul.allow_tf32 = False
         self.groups: dict[int, dict] = {}
         self.lib = lib()
+        self.gate = _CaptureGate()
 
     # ---- batched launches (one per cluster size), optionally graphed ----
     def _group(self, key) -> dict:
@@ -210,18 +256,20 @@ class Server:
             self._launch(key, g)
         else:
             if g["graph"] is None:
-                # warm the kernel variant outside capture, on empty slots
-                scratch = torch.zeros_like(g["items"])
-                save = g["items"]
-                g["items"] = scratch
-                self._launch(key, g)
-                g["items"] = save
-                torch.cuda.synchronize(self.dev)
-                graph = torch.cuda.CUDAGraph()
-                # admission threads keep launching on their streams meanwhile
-                with torch.cuda.graph(graph, stream=torch.cuda.Stream(self.dev),
-                                      capture_error_mode="thread_local"):
+                # no admission thread issues CUDA work during the capture
+                with self.gate.exclusive():
+                    # warm the kernel variant outside capture, on empty slots
+                    scratch = torch.zeros_like(g["items"])
+                    save = g["items"]
+                    g["items"] = scratch
                     self._launch(key, g)
+                    g["items"] = save
+                    torch.cuda.synchronize(self.dev)
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph,
+                                          stream=torch.cuda.Stream(self.dev),
+                                          capture_error_mode="thread_local"):
+                        self._launch(key, g)
                 g["graph"] = graph
                 # the captured launch reads the item array when replayed
                 g["items"].copy_(g["host"], non_blocking=True)
@@ -271,39 +319,41 @@ class Server:
     # ---- request lifecycle ----
     def _admit(self, rq: Request):
         """Runs on an admission thread: draw A and the initial factors and
-        compress, all on a free side stream."""
+        compress, all on a free side stream, outside any graph capture of
+        the serving thread (the gate's shared side)."""
         import synth
         slot = self.free.get()
         try:
-            rq.stream_idx = slot
-            s = self.side[slot]
-            with torch.cuda.stream(s):
-                rq.A = synth.lowrank_torch(rq.m, rq.n, rq.r, rq.sigma, rq.seed,
-                                           device=self.dev)
-                U0, Vt0 = synth.init_torch(rq.m, rq.n, rq.r, rq.seed + 1,
-                                           device=self.dev)
-                nb = self.lib.cnmf_compress_workspace(rq.m, rq.n, rq.d, 1)
-                ws = self.comp_ws[slot]
-                if ws is None or ws.numel() < nb:
-                    ws = torch.empty(int(nb * 1.25) + 256, dtype=torch.uint8,
-                                     device=self.dev)
-                    self.comp_ws[slot] = ws
-                L, Rt, At, _ = cnmf_compress(rq.A, rq.r, rq.d, rq.q,
-                                             rq.seed + 2, status=self.status,
-                                             ws=ws)
-                rq.problem = BatchProblem(L, Rt, At, U0, Vt0, 1.0, 1.0)
-                if self.stop_at_target:
-                    # A-tilde to the host for the target (an asynchronous
-                    # copy: nothing here may synchronise while the main
-                    # thread captures a graph)
-                    rq.At_host = torch.empty(At.shape, dtype=At.dtype,
-                                             pin_memory=True)
-                    rq.At_host.copy_(At, non_blocking=True)
-                rq.event = torch.cuda.Event()
-                rq.event.record(s)
+            with self.gate.shared():
+                rq.stream_idx = slot
+                s = self.side[slot]
+                with torch.cuda.stream(s):
+                    rq.A = synth.lowrank_torch(rq.m, rq.n, rq.r, rq.sigma,
+                                               rq.seed, device=self.dev)
+                    U0, Vt0 = synth.init_torch(rq.m, rq.n, rq.r, rq.seed + 1,
+                                               device=self.dev)
+                    nb = self.lib.cnmf_compress_workspace(rq.m, rq.n, rq.d, 1)
+                    ws = self.comp_ws[slot]
+                    if ws is None or ws.numel() < nb:
+                        ws = torch.empty(int(nb * 1.25) + 256,
+                                         dtype=torch.uint8, device=self.dev)
+                        self.comp_ws[slot] = ws
+                    L, Rt, At, _ = cnmf_compress(rq.A, rq.r, rq.d, rq.q,
+                                                 rq.seed + 2,
+                                                 status=self.status, ws=ws)
+                    rq.problem = BatchProblem(L, Rt, At, U0, Vt0, 1.0, 1.0)
+                    if self.stop_at_target:
+                        # A-tilde to the host for the target (asynchronous)
+                        rq.At_host = torch.empty(At.shape, dtype=At.dtype,
+                                                 pin_memory=True)
+                        rq.At_host.copy_(At, non_blocking=True)
+                    rq.event = torch.cuda.Event()
+                    rq.event.record(s)
         finally:
             self.free.put(slot)
-        rq.cluster_size = self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
+        # the autotuner may time kernels on the device for a new size bucket
+        with self.gate.shared():
+            rq.cluster_size = self.tuner.cluster_size(rq.m, rq.n, rq.r, rq.d)
 
     def _ready(self, rq: Request, now: float):
         # penalty: lambda = phi = penalty_scale ||Atilde||_F / r, formed by

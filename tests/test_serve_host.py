@@ -43,3 +43,53 @@ def test_autotune_buckets():
     assert bucket(1024, 1025, 16, 33) == "m1024_n2048_r16_d64"
     assert bucket(3000, 200, 20, 30) == bucket(2100, 1, 17, 31)
 
+
+
+def test_capture_gate_excludes_admissions():
+    """The serving thread's graph capture (exclusive) never overlaps an
+    admission thread's CUDA work (shared); a waiting capture holds back new
+    admissions, and several admissions run together."""
+    import threading
+    import time
+    from paper_1505_04650_gb300.serve import _CaptureGate
+    gate = _CaptureGate()
+    log, lock = [], threading.Lock()
+    inside = {"shared": 0, "excl": 0, "max_shared": 0, "overlap": False}
+
+    def admit(k):
+        with gate.shared():
+            with lock:
+                inside["shared"] += 1
+                inside["max_shared"] = max(inside["max_shared"],
+                                           inside["shared"])
+                inside["overlap"] |= inside["excl"] > 0
+            time.sleep(0.05)
+            with lock:
+                inside["shared"] -= 1
+                log.append(("a", k))
+
+    def capture():
+        with gate.exclusive():
+            with lock:
+                inside["excl"] += 1
+                inside["overlap"] |= inside["shared"] > 0
+            time.sleep(0.05)
+            with lock:
+                inside["excl"] -= 1
+                log.append(("c", 0))
+
+    ts = [threading.Thread(target=admit, args=(k,)) for k in range(3)]
+    for t in ts:
+        t.start()
+    time.sleep(0.01)
+    tc = threading.Thread(target=capture)
+    tc.start()
+    time.sleep(0.01)
+    late = threading.Thread(target=admit, args=(9,))   # arrives while the
+    late.start()                                       # capture waits
+    for t in ts + [tc, late]:
+        t.join(timeout=10)
+    assert not inside["overlap"]
+    assert inside["max_shared"] >= 2
+    # the capture ran before the late admission
+    assert log.index(("c", 0)) < log.index(("a", 9))
