@@ -19,10 +19,10 @@
 // into two bf16 tiles, A_hi = bf16(A) and A_lo = bf16(A - A_hi), both
 // rounded to nearest, so |A - A_hi - A_lo| <= 2^-18 |A|; both products take
 // both terms.  X and Y (FP32) are split the same way into bf16 hi | lo
-// planes, packed transposed (the K-major B operand).  Both products place
-// them side by side along N (N = 2 KP), so one MMA per K-chunk forms the
-// hi and lo products together (each MMA reads the A slice once) and the
-// epilogue adds the halves.  Every product of two bf16 values is exact in FP32, so
+// planes, packed transposed (the K-major B operand).  A X places them side
+// by side along N (N = 2 KP), so one MMA forms A X_hi and A X_lo together
+// and the epilogue adds the halves; A^T Y adds them in its accumulator
+// through two MMAs.  Every product of two bf16 values is exact in FP32, so
 // the result is (A_hi + A_lo)(X_hi + X_lo) up to FP32 accumulation, minus,
 // for FP32 A, the term A_lo Y_lo of A^T Y (below 2^-18 of |A||Y|).
 //
@@ -74,12 +74,13 @@ struct FuCfg {
   static constexpr int STAGES = ST_FIT > 4 ? 4 : ST_FIT;
   static constexpr size_t SMEM =
       1024 + (size_t)STAGES * STAGE + (size_t)YBUF * P_BYTES;
-  // A X accumulators (two, double-buffered) and the A^T Y accumulators
-  // (one per column of a group) hold the hi and lo parts side by side
-  // (N = 2 KP: one MMA per K-chunk and term of A), so tensor memory holds
-  // (512 - 4 KP) / (2 KP) A^T Y accumulators
+  // A X accumulators (two, double-buffered) hold the hi and lo parts side
+  // by side (N = 2 KP: one MMA per K-chunk and term); the A^T Y
+  // accumulators (one per column of a group) take the hi and lo parts
+  // through two MMAs into KP columns, so tensor memory holds
+  // (512 - 4 KP) / KP of them -- fewer A X partials
   static constexpr int ZX = 2 * KP;
-  static constexpr int ZY = 2 * KP;
+  static constexpr int ZY = KP;
   static constexpr int NCONV = F32 ? 16 : 0;    // converter warps
   static constexpr int NT = 256 + 32 * NCONV;
   static_assert(STAGES >= 2, "fused pass needs two stages");
@@ -225,8 +226,7 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
   constexpr int ST = C::STAGES;
   constexpr int YB = C::YBUF;
   constexpr uint32_t ID_X = idesc_mk(FU_T, C::ZX, false, false);
-  constexpr uint32_t ID_T = idesc_mk(FU_T, C::ZY, true, false);   // hi | lo
-  constexpr uint32_t ID_T1 = idesc_mk(FU_T, KP, true, false);     // hi only
+  constexpr uint32_t ID_T = idesc_mk(FU_T, C::ZY, true, false);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[4], conv_bar[4], empty_bar[4];
   __shared__ __align__(8) uint64_t y_full[2], y_empty[2];
@@ -367,10 +367,9 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
     // segment, double-buffered), warp 3 forms A^T Y (accumulators Z2, one
     // per column of the group).  Each releases a stage with its own commit,
     // so the two MMA streams are issued side by side from two SM
-    // sub-partitions.  Per K-chunk of 16: one A X MMA per bf16 term of A on
-    // the panel's hi | lo rows; one A^T Y MMA of A_hi on the panel's hi | lo
-    // rows and, for FP32 A, one of A_lo on the hi rows (A_lo Y_lo, below
-    // 2^-18 of |A||Y|, is left out).
+    // sub-partitions.  Per K-chunk of 16 and per bf16 term of A: one A X
+    // MMA on the panel's hi | lo rows; A^T Y MMAs on the hi rows and on the
+    // lo rows (FP32 A: A_lo Y_lo, below 2^-18 of |A||Y|, is left out).
     const bool is_x = warp == 1;
     if ((is_x && hx) || (!is_x && hy)) {
       int s = 0, zb = 0, yb = 0;
@@ -444,14 +443,14 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
             const uint64_t pk =
                 (uint64_t)(((kc >> 2) * C::P_BOX + (kc & 3) * 32) >> 4);
             const uint64_t tk = (uint64_t)((kc * 16 * 128) >> 4);
-            // A_hi [Y_hi | Y_lo] in one MMA (N = 2 KP, the panel's hi and
-            // lo rows side by side, as in A X); FP32 A adds A_lo Y_hi into
-            // the hi half
-            tc_mma(z2, dAt + tk, dY + pk, ID_T,
-                   (fresh2 && kc == 0) ? 0u : 1u);
-            if (F32)
-              tc_mma(z2, dAt + (uint64_t)(C::LO_OFF >> 4) + tk, dY + pk,
-                     ID_T1, 1u);
+#pragma unroll
+            for (int t = 0; t < C::NTERM; ++t) {
+              const uint64_t a = dAt + (uint64_t)((t * C::LO_OFF) >> 4) + tk;
+              tc_mma(z2, a, dY + pk, ID_T,
+                     (fresh2 && kc == 0 && t == 0) ? 0u : 1u);
+              if (t == 0)
+                tc_mma(z2, a, dY + pk + (uint64_t)(C::P_LO >> 4), ID_T, 1u);
+            }
           }
           touched |= 1u << p.jl;
           tc_commit(&empty_bar[s]);
@@ -568,11 +567,7 @@ __global__ void __launch_bounds__((FuCfg<KP, F32>::NT), 1)
           for (int c0 = 0; c0 < KP; c0 += 16) {
             float v[16];
             if (t_on) {
-              float lo[16];
-              tc_ld16(zt + c0, v);            // A Y_hi (+ A_lo Y_hi)
-              tc_ld16(zt + KP + c0, lo);      // A_hi Y_lo
-#pragma unroll
-              for (int t = 0; t < 16; ++t) v[t] += lo[t];
+              tc_ld16(zt + c0, v);
             } else {
 #pragma unroll
               for (int t = 0; t < 16; ++t) v[t] = 0.0f;
@@ -741,7 +736,7 @@ static FuPlan fu_plan(int64_t m, int64_t n, int k, cnmf_dtype a_type,
   if (m >= (1ll << 31) || n >= (1ll << 31)) return pl;
   pl.f32 = a_type == CNMF_F32;
   pl.KP = k <= 16 ? 16 : 32;
-  const int ZX = 2 * pl.KP, ZY = 2 * pl.KP;   // FuCfg::ZX, FuCfg::ZY
+  const int ZX = 2 * pl.KP, ZY = pl.KP;   // FuCfg::ZX, FuCfg::ZY
   FuGeom& q = pl.geo;
   q.has_x = has_x ? 1 : 0;
   q.has_y = has_y ? 1 : 0;
