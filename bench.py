@@ -1027,6 +1027,7 @@ def time_to_target(cn, A, U0, Vt0, ws_c, ws_f, st, stream, noiseless=False,
     if comp.get("seconds") and plain.get("seconds"):
         out["speedup_vs_plain"] = plain["seconds"] / comp["seconds"]
     if not alg2:
+        cn.raise_on_status(st, "time to target")
         return out
     # ---- compressed alternating NMF (Alg. 2): exact NNLS steps and
     # multiplicative updates, from (0, V0) and (U0, V0)
