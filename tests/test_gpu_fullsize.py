@@ -212,3 +212,37 @@ def test_cnmf_bench_size_matches_oracle():
     ev = rel(to_np(Vt).T, ref.V)
     print(f"20 sweeps: U {eu:.2e}, V {ev:.2e}")
     assert eu <= 1e-4 and ev <= 1e-4
+
+
+def test_noiseless_bench_size_rank_deficient():
+    """The bench shape without noise (A = X0 Y0 exactly: rank r = 20 below
+    the sketch size d = 30, FP32): the compression must still return
+    orthonormal L and R^T (the null directions are an arbitrary orthonormal
+    completion) that capture A, A = L A-tilde R to FP32 rounding, and the
+    compressed ADMM must reach rho <= 1e-3 as the FP64 oracle does on the
+    same A (5.5e-4 after 200 sweeps at lambda = ||A-tilde|| / r).  The
+    shifted first CholeskyQR sweep of each pass and the final unshifted
+    one both meet a numerically rank-deficient panel here."""
+    torch = need_gpu()
+    import paper_1505_04650_gb300 as cn
+    m, n, r, d, q = 20000, 10000, 20, 30, 4
+    A = torch.from_numpy(synth.lowrank(m, n, r, 0.0, 1001,
+                                       dtype=np.float32)).cuda()
+    L, Rt, At, st = cn.cnmf_compress(A, r, d, q, 2001)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    I = torch.eye(d, dtype=torch.float64, device="cuda")
+    for P in (L, Rt):
+        P = P.double()
+        assert float(torch.linalg.norm(P.t() @ P - I)) <= 1e-4
+    Ad = A.double()
+    cap = torch.linalg.norm(Ad - (L.double() @ At.double()) @ Rt.double().t())
+    assert float(cap / torch.linalg.norm(Ad)) <= 1e-5
+    U0, V0 = synth.init_factors(m, n, r, 3001)
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    Vt = torch.tensor(V0.T.copy(), dtype=torch.float32, device="cuda")
+    lam = float(torch.linalg.norm(At.double())) / r
+    cn.cnmf_factor(L, Rt, At, U, Vt, lam, lam, 400, status=st)
+    e2, a2 = cn.cnmf_residual(A, U, Vt).cpu().tolist()
+    cn.raise_on_status(st, "noiseless factor")
+    assert math.sqrt(e2 / a2) <= 1e-3
