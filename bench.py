@@ -949,7 +949,7 @@ def time_to_target(cn, A, U0, Vt0, ws_c, ws_f, st, stream, noiseless=False,
 
     The penalties are not given by the paper (Alg. 4); each ADMM -- the
     compressed one and the plain, uncompressed one on the same GPU -- runs
-    at its best of lambda = phi = c ||M||_F / r, c in {0.1, 0.3, 1}, M =
+    at its best of lambda = phi = c ||M||_F / r, c in {0.03, 0.1, 0.3, 1, 3}, M =
     A-tilde or A.  Alg. 2 (exact NNLS steps and multiplicative updates)
     needs no penalty."""
     import torch

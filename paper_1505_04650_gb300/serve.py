@@ -22,9 +22,13 @@ server
   rho = ||A - U V||_F / ||A||_F at or below tau = rho* + 1e-3, where rho*
   is the residual of the rank-r truncation of the request's compressed
   matrix lifted back to m x n (formed when the request joins).  rho is
-  computed (cnmf_residual) every `check_every` sweeps between rounds; a
+  computed every `check_every` sweeps between rounds, for all requests due
+  in one launch (cnmf_residual_batched) read back with one copy; a
   request that reaches `max_sweeps` first leaves too and is counted as not
   at target;
+* captures each batch group's CUDA graph with the admission threads held
+  back (a shared/exclusive gate), so no other thread's CUDA call lands
+  inside a capture;
 * on completion keeps the relative residual and frees the request's
   memory.
 
